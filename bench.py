@@ -1,0 +1,361 @@
+"""Benchmark: exact PPSP queries/sec and GTEPS on one GB300.
+
+Workload (default): the road-like 1024 x 1024 jittered grid (about 1.05 M
+vertices, 10% of grid edges deleted, 0.5% shortcuts of at most 20 cells,
+weights round(1000 * length)) with 1,000 queries split into near/mid/far
+thirds by grid distance, answered with bidirectional A* (Sec. 4.5) as one
+batch (Multi-BiDS schedule, Sec. 5.2).  A step is one pass of the whole batch.
+
+Reported:
+  value        queries/sec with the graph, the pairs and the output in HBM
+               (CUDA events on the launching stream around each step; the L2
+               is flushed between steps by writing a 256 MB buffer)
+  e2e          queries/sec through ppsp_batch with host buffers (query graph
+               build, host->device copy of the pairs, search, device->host
+               copy of the distances inside the timed region)
+  plain        the same queries one at a time on the whole GPU (Plain-BiDS)
+  roofline     algorithmic bytes of the engine kernel per step / step time
+  cpu_baseline the CPU Dijkstra oracle on a bounded sample, all host cores
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_workload(cfg: int):
+    from workloads import config_workload
+
+    wl = config_workload(cfg)
+    pairs = next(iter(wl["batches"].values()))
+    mode = {"bids": "bids", "bidastar": "bidastar", "multi_astar": "bidastar", "serving": "bids"}[wl["mode"]]
+    return wl, pairs, mode
+
+
+def algorithmic_bytes(cnt: dict, dist_bytes: int, astar: bool) -> int:
+    """Bytes the method must touch (offsets, edges, distances, queue entries)."""
+    X, E, R, P, T = cnt["extracted"], cnt["edges"], cnt["relaxed"], cnt["pushed"], cnt["touched"]
+    coord = 8 if astar else 0
+    return int(X * (2 * 4 + dist_bytes + coord) + E * (4 + 4 + dist_bytes) + R * (dist_bytes + coord)
+               + P * 4 * 2 + T * dist_bytes)
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def engine_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2506_16488_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2506_16488_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(workload: str):
+    """DRAM bytes per engine launch from the committed ncu summary, if it
+    was taken on the current sources; else None."""
+    p = os.path.join(ROOT, "profiles", "engine_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != engine_source_hash() or d.get("workload") != workload:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(g, pairs, labels, budget_s: float = 20.0):
+    import oracle
+
+    threads = os.cpu_count() or 1
+    # a bounded, stratified sample: equal numbers of near, mid and far queries
+    rng = np.random.default_rng(7)
+    per = max(1, min(20, threads * 2))
+    idx = np.concatenate([rng.choice(np.nonzero(labels == b)[0], size=per, replace=False) for b in range(3)])
+    sample = pairs[idx]
+    t0 = time.perf_counter()
+    oracle.pairs_threaded(g.offsets, g.targets, g.weights, sample, threads)
+    dt = time.perf_counter() - t0
+    return {"value": sample.shape[0] / dt, "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": f"{sample.shape[0]} queries ({per} near/mid/far each) of the 1,000, one Dijkstra "
+                      f"per query, {threads} threads"}
+
+
+def run_reference(args):
+    """The CPU oracle timed as the reference arm (rank 0 only)."""
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    import oracle
+
+    wl, pairs, mode = load_workload(args.config)
+    g = wl["graph"]
+    labels = wl.get("labels", np.zeros(pairs.shape[0], dtype=np.int32))
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(11)
+    per = max(1, min(6, threads // 2))
+    times = []
+    nq = 0
+    for step in range(args.warmup + args.steps):
+        idx = np.concatenate([rng.choice(np.nonzero(labels == b)[0], size=per, replace=False)
+                              for b in np.unique(labels)])
+        t0 = time.perf_counter()
+        oracle.pairs_threaded(g.offsets, g.targets, g.weights, pairs[idx], threads)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            nq += idx.shape[0]
+    total = sum(times)
+    value = nq / total
+    line = {
+        "impl": "reference", "metric": "PPSP queries/sec (exact distances)", "value": value,
+        "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "road-like 1024x1024 grid, 1000 near/mid/far queries",
+                   "sample_per_step": int(idx.shape[0])},
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{idx.shape[0]} stratified queries per step, binary-heap Dijkstra, "
+                                   f"{threads} threads"},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2506_16488_gb300 import ppsp
+
+    wl, pairs, mode = load_workload(args.config)
+    g = wl["graph"]
+    k = pairs.shape[0]
+    workload = "road-like 1024x1024 grid (%d vertices, %d CSR entries), %d near/mid/far queries, %s" % (
+        g.n, g.m, k, mode)
+    G = ppsp.Graph.from_csr(g)
+    stream = torch.cuda.Stream()
+    opts = dict(mode=mode, strategy="multi", stream=stream.cuda_stream)
+    if args.delta:
+        opts["delta"] = args.delta
+    plan = G.plan(pairs, **opts)
+    out = torch.zeros(k, dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        plan.run(out.data_ptr())
+
+    for _ in range(args.warmup):
+        step()
+        cnt = plan.sync()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    counters = []
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        counters.append(plan.sync())
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    got = out.cpu().numpy().view(np.uint64)
+
+    # e2e through the C ABI with host buffers
+    e2e_ms = []
+    for i in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = G.batch(pairs, mode=mode, strategy="multi", **({"delta": args.delta} if args.delta else {}))
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+    assert np.array_equal(res, got)
+
+    # plain: one query at a time on the whole GPU
+    plain_plan = G.plan(pairs, mode=mode, strategy="plain", stream=stream.cuda_stream,
+                        **({"delta": args.delta} if args.delta else {}))
+    plain_out = torch.zeros(k, dtype=torch.int64, device="cuda")
+    plain_plan.run(plain_out.data_ptr())
+    plain_plan.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plain_plan.run(plain_out.data_ptr())
+    e1.record(stream)
+    plain_cnt = plain_plan.sync()
+    plain_ms = e0.elapsed_time(e1)
+    assert np.array_equal(plain_out.cpu().numpy().view(np.uint64), got)
+
+    if rank != 0:
+        return
+    cnt = counters[-1]
+    astar = mode in ("bidastar", "astar")
+    alg_bytes = algorithmic_bytes(cnt, 4, astar)
+    ms_per_step = total_ms / args.steps
+    qps = world * k * args.steps / (total_ms / 1000.0)
+    peak, peak_kind = read_peaks()
+    achieved = alg_bytes / (ms_per_step / 1000.0) / 1e9
+    cpu = cpu_baseline(g, pairs, wl.get("labels", np.zeros(k, dtype=np.int32))) if world == 1 else None
+    line = {
+        "metric": "PPSP queries/sec (exact distances), batched vs plain one-at-a-time",
+        "value": qps,
+        "unit": "queries/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": workload, "queries_per_step": k, "strategy": "multi (query graph)",
+                   "delta": args.delta or "default (mean edge weight)",
+                   "l2": "flushed between steps (256 MB write)",
+                   "inputs": "plan (query graph, schedule) built before the timed region; graph, plan and "
+                             "output resident in HBM", "parallelism": f"replicas x{world}"},
+        "gteps": cnt["edges"] / (ms_per_step / 1000.0) / 1e9,
+        "plain": {"value": k / (plain_ms / 1000.0), "unit": "queries/s", "ms": plain_ms,
+                  "gteps": plain_cnt["edges"] / (plain_ms / 1000.0) / 1e9},
+        "speedup_vs_plain": qps / world / (k / (plain_ms / 1000.0)),
+        "counters": cnt,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": read_traffic(workload),
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "e2e": {"value": world * k / (float(np.median(e2e_ms)) / 1000.0), "unit": "queries/s",
+                "h2d_bytes_per_step": int(pairs.nbytes), "d2h_bytes_per_step": int(k * 8)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    plain_plan.close()
+    G.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--delta", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

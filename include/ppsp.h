@@ -1,0 +1,243 @@
+/*
+ * ppsp.h -- C ABI of the GB300 point-to-point shortest-path (PPSP) library.
+ *
+ * The library answers exact s-t distance queries on a device-resident CSR graph
+ * with the paper's stepping-style PPSP framework (Alg. 2): a frontier is
+ * processed in steps under an advancing threshold (Alg. 1, Delta*-stepping,
+ * Sec. 2), with the Init / Prune / UpdateDistance plug-ins of Table 2 for
+ * early termination (ET, Sec. 4.2), A* (Sec. 4.3), bidirectional search (BiDS,
+ * Sec. 4.4, Theorem 4.1) and bidirectional A* (BiD-A*, Sec. 4.5, Theorem 4.2),
+ * and batches of queries organised as a query graph (Sec. 5.1) and searched
+ * with Multi-BiDS (Sec. 5.2).  All arithmetic on distances is integer, so
+ * results are exact.  The paper defines no programming interface; names and
+ * layouts here are this library's own.
+ *
+ * Conventions for every entry point:
+ *  - Every function returns a ppsp_status; nothing aborts or throws across the
+ *    ABI.  A device-side failure (a bounded wait that ran out, a distance that
+ *    does not fit the chosen width) comes back as a status, and the library
+ *    stays usable afterwards.
+ *  - "host" pointers are ordinary CPU memory owned by the caller and only read
+ *    or written during the call.  "device" pointers are CUDA global memory on
+ *    the graph's device, owned by the caller.
+ *  - Unreachable targets have distance PPSP_INF (UINT64_MAX) and a path
+ *    length of 0.
+ *  - A graph object may be used from one host thread at a time.
+ */
+#ifndef PPSP_H
+#define PPSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PPSP_INF UINT64_MAX
+
+typedef struct ppsp_graph ppsp_graph;
+typedef struct ppsp_plan ppsp_plan;
+
+typedef enum {
+    PPSP_OK = 0,
+    PPSP_ERR_INVALID_ARG = 1,      /* null pointer, id >= n, bad option value */
+    PPSP_ERR_BAD_GRAPH = 2,        /* malformed CSR, asymmetric "undirected" graph */
+    PPSP_ERR_OOM = 3,              /* device or host allocation failed */
+    PPSP_ERR_CUDA = 4,             /* a CUDA runtime call failed (no device, launch error) */
+    PPSP_ERR_TIMEOUT = 5,          /* a bounded device-side wait ran out of iterations */
+    PPSP_ERR_NO_COORDS = 6,        /* A* mode on a graph created without coordinates */
+    PPSP_ERR_BUFFER_TOO_SMALL = 7, /* a path did not fit; the needed length is reported */
+    PPSP_ERR_OVERFLOW = 8,         /* a distance does not fit 32 bits (use dist_bits = 64) */
+    PPSP_ERR_UNSUPPORTED = 9       /* valid request outside what this build supports */
+} ppsp_status;
+
+/* Search plug-ins (Table 2). */
+enum {
+    PPSP_BIDS = 0,     /* bidirectional search, prune 2*d >= mu (Sec. 4.4)            */
+    PPSP_BIDASTAR = 1, /* bidirectional A*, average potential h_F = -h_B (Sec. 4.5)   */
+    PPSP_ET = 2,       /* one-directional with early termination, prune d >= mu       */
+    PPSP_ASTAR = 3     /* one-directional A*, prune d + h_t(v) >= mu (Sec. 4.3)       */
+};
+
+/* Graph flags. */
+enum { PPSP_UNDIRECTED = 1u };
+
+/* Frontier representation policy (App. B "Sparse-Dense Optimization"). */
+enum { PPSP_FRONTIER_AUTO = 0, PPSP_FRONTIER_SPARSE = 1, PPSP_FRONTIER_DENSE = 2 };
+
+/* Layout of the per-search tentative-distance arrays of one batch group. */
+enum { PPSP_LAYOUT_AUTO = 0, PPSP_LAYOUT_INTERLEAVED = 1, PPSP_LAYOUT_STACKED = 2 };
+
+/* How a batch is executed (Sec. 5.2 and the batch baselines of Sec. 7). */
+enum {
+    PPSP_BATCH_MULTI = 0,      /* Multi-BiDS: one search per query-graph vertex, shared  */
+    PPSP_BATCH_PLAIN_STAR = 1, /* Plain*: every query its own pair of searches, all at once */
+    PPSP_BATCH_PLAIN = 2       /* Plain: one query at a time, each on the whole GPU       */
+};
+
+/*
+ * Query options.  Call ppsp_options_init() first; it fills in the defaults
+ * noted beside each field.  Options never change answers, only speed
+ * (Theorems 4.1 and 4.2 hold for any stepping schedule), except mode, which
+ * selects the plug-in, and dist_bits, which bounds representable distances.
+ */
+typedef struct {
+    int32_t mode;            /* PPSP_BIDS (default) ... PPSP_ASTAR                         */
+    int32_t dist_bits;       /* 32 (default) or 64: width of tentative distances in HBM     */
+    uint64_t delta;          /* stepping increment Delta >= 1; 0 = auto (learned model if
+                                attached to the graph, else mean edge weight)               */
+    int32_t frontier;        /* PPSP_FRONTIER_* (default AUTO)                              */
+    int32_t layout;          /* PPSP_LAYOUT_* (default AUTO)                                */
+    int32_t batch_strategy;  /* PPSP_BATCH_* (default MULTI)                                */
+    int32_t block_threads;   /* 256, 512 or 1024 threads per CTA; 0 = auto                 */
+    int32_t team_ctas;       /* CTAs cooperating on one small group (pair); 0 = auto        */
+    int32_t big_team_ctas;   /* CTAs cooperating on one multi-search group; 0 = auto        */
+    uint32_t dense_den;      /* frontier goes dense above (searches * n) / dense_den; 0=auto */
+    int32_t want_paths;      /* 1: also return one shortest path per query (weights >= 1)   */
+    int32_t max_ctas;        /* cap on resident CTAs used (0 = all that fit)               */
+    uint64_t spin_limit;     /* iterations of a device-side wait before PPSP_ERR_TIMEOUT;
+                                0 = default (about a few seconds)                          */
+    void* stream;            /* cudaStream_t to run on; NULL = the legacy default stream    */
+    uint32_t debug_flags;    /* test hooks, 0 in normal use (PPSP_DEBUG_*)                  */
+    uint32_t reserved[7];
+} ppsp_options;
+
+/* Test hook: device barriers wait for one arrival that never comes, so every
+ * multi-CTA wait runs out and the call returns PPSP_ERR_TIMEOUT. */
+#define PPSP_DEBUG_BARRIER_NEVER_RELEASES 1u
+
+/* Work counters of one call (paper Sec. 7 measures time; these feed GTEPS and
+ * the algorithmic-bytes roofline). */
+typedef struct {
+    uint64_t extracted;   /* frontier entries taken and not pruned (X)           */
+    uint64_t edges;       /* adjacency entries scanned (E)                        */
+    uint64_t relaxed;     /* successful WriteMin relaxations (R)                  */
+    uint64_t pushed;      /* frontier insertions (P)                              */
+    uint64_t rounds;      /* stepping rounds summed over groups                   */
+    uint64_t groups;      /* searched groups (pairs or query-graph components)    */
+    uint64_t searches;    /* single-source searches                               */
+    uint64_t touched;     /* tentative distances that left infinity               */
+    uint64_t dense_rounds;/* rounds whose frontier was a bitmap                   */
+    uint64_t reserved[7];
+} ppsp_counters;
+
+/* Graph properties computed at creation. */
+typedef struct {
+    uint64_t n, m;
+    uint64_t w_min, w_max;
+    double w_mean, w_std;
+    uint64_t deg_max;
+    double potential_scale;   /* c of the A* potential (0 if no coordinates)            */
+    int32_t potential_shift;  /* fixed-point bits F of the potential coordinates        */
+    int32_t has_coords;
+    int32_t undirected;
+    int32_t has_zero_weight;
+    uint64_t device_bytes;    /* device memory held by the graph (CSR + coordinates)    */
+} ppsp_graph_info;
+
+/* Fill *o with defaults.  Never fails for a non-null o. */
+void ppsp_options_init(ppsp_options* o);
+
+/* Static string for a status code. */
+const char* ppsp_status_string(ppsp_status s);
+
+/* Text of the last CUDA failure seen by the calling thread ("" if none);
+ * valid until the thread's next library call. */
+const char* ppsp_last_error_detail(void);
+
+/*
+ * Create a device-resident graph from a host CSR (paper Sec. 2: G = (V, E, w),
+ * w: E -> R+, here non-negative uint32).
+ *   n        number of vertices, 1 <= n < 2^32 - 1
+ *   m        number of adjacency entries (an undirected edge counts twice), m < 2^32
+ *   offsets  host uint64[n+1], offsets[0] = 0, non-decreasing, offsets[n] = m
+ *   targets  host uint32[m], every id < n
+ *   weights  host uint32[m]
+ *   coords   host float[2n] (x, y per vertex) or NULL; needed by the A* modes
+ *   flags    PPSP_UNDIRECTED: the CSR is symmetric with equal weights both ways
+ *            (validated; the bidirectional modes search backwards on the same CSR)
+ * Inputs are copied; the caller may free them after the call.  On success
+ * *out owns device memory until ppsp_graph_destroy.
+ * Errors: INVALID_ARG (null pointers, n or m out of range), BAD_GRAPH
+ * (malformed or asymmetric CSR), OOM, CUDA.
+ */
+ppsp_status ppsp_graph_create(uint64_t n, uint64_t m, const uint64_t* offsets,
+                              const uint32_t* targets, const uint32_t* weights,
+                              const float* coords, uint32_t flags, ppsp_graph** out);
+
+/* Free the graph and every buffer the library allocated for it.  NULL is a no-op. */
+void ppsp_graph_destroy(ppsp_graph* g);
+
+/* Copy the graph's properties into *out (host). */
+ppsp_status ppsp_graph_get_info(const ppsp_graph* g, ppsp_graph_info* out);
+
+/*
+ * One query d(s, t) with the plug-in of opt->mode (NULL opt = defaults), on
+ * the whole GPU ("Plain" execution of one query, Sec. 5.2).
+ *   dist_out  host uint64, receives d(s, t) or PPSP_INF
+ *   path_buf  host uint32[path_cap] or NULL; with opt->want_paths it receives
+ *             one shortest path s..t (s == t gives [s])
+ *   path_len  host uint64 or NULL; receives the number of vertices of the path
+ *             (0 if unreachable), also when the path did not fit (then the
+ *             status is BUFFER_TOO_SMALL and dist_out is still valid)
+ * Errors: INVALID_ARG (s or t >= n, bad options), NO_COORDS, UNSUPPORTED
+ * (bidirectional mode on a directed graph; paths on a graph with zero-weight
+ * edges), OOM, CUDA, TIMEOUT, OVERFLOW.
+ */
+ppsp_status ppsp_query(ppsp_graph* g, uint32_t s, uint32_t t, const ppsp_options* opt,
+                       uint64_t* dist_out, uint32_t* path_buf, uint64_t path_cap,
+                       uint64_t* path_len);
+
+/*
+ * A batch of k queries (Sec. 5): pairs is host uint32[2k] (s0, t0, s1, t1, ...).
+ * The batch is turned into a query graph G_q (Sec. 5.1; repeated and reversed
+ * pairs collapse to one query edge) and run with opt->batch_strategy.
+ *   dists_out     host uint64[k], answer of each pair in input order
+ *   paths_buf     host uint32 buffer or NULL (needs opt->want_paths)
+ *   path_offsets  host uint64[k+1] or NULL: query q may use
+ *                 paths_buf[path_offsets[q] .. path_offsets[q+1])
+ *   path_lens     host uint64[k] or NULL: vertices on each path (needed length
+ *                 if it did not fit; then the call returns BUFFER_TOO_SMALL)
+ *   counters      host ppsp_counters or NULL: work done by the call
+ * k = 0 is valid and does nothing.  Errors as ppsp_query.
+ */
+ppsp_status ppsp_batch(ppsp_graph* g, const uint32_t* pairs, uint64_t k, const ppsp_options* opt,
+                       uint64_t* dists_out, uint32_t* paths_buf, const uint64_t* path_offsets,
+                       uint64_t* path_lens, ppsp_counters* counters);
+
+/*
+ * Split form of ppsp_batch for callers that keep results in device memory and
+ * replay the same batch shape: ppsp_plan_create does the host-side work (query
+ * graph, groups, schedule, device descriptors, search memory), ppsp_plan_run
+ * launches the searches on opt->stream and writes d_dists_out (device
+ * uint64[k], input order) before the stream's next work; ppsp_plan_sync waits
+ * for the stream and returns the run's device status and counters.  A plan
+ * keeps device memory until ppsp_plan_destroy and belongs to its graph.
+ * Paths are not available through plans (use ppsp_batch).
+ */
+ppsp_status ppsp_plan_create(ppsp_graph* g, const uint32_t* pairs, uint64_t k,
+                             const ppsp_options* opt, ppsp_plan** out);
+ppsp_status ppsp_plan_run(ppsp_plan* p, uint64_t* d_dists_out);
+ppsp_status ppsp_plan_sync(ppsp_plan* p, ppsp_counters* counters);
+void ppsp_plan_destroy(ppsp_plan* p);
+
+/*
+ * A* potential of the graph (Sec. 4.3; consistency, Fact 4.1).  The library
+ * stores integer potential coordinates P(v) = floor(p(v) * c * 2^F + 0.5)
+ * (float64 arithmetic, c and F in ppsp_graph_info) chosen at creation so that
+ * |P(u) - P(v)|^2 <= (2^F * w(u,v))^2 on every edge; the potential is
+ * h_x(v) = floor(|P(v) - P(x)| / 2^F), computed exactly in integers.
+ *   ppsp_potential_coords: host int64[2n] receives P (x, y per vertex).
+ *   ppsp_potential_eval:   evaluates h_anchor(v) on the device for the host
+ *                          uint32 vertices[count], into host int64 out[count].
+ * Errors: NO_COORDS, INVALID_ARG, CUDA.
+ */
+ppsp_status ppsp_potential_coords(const ppsp_graph* g, int64_t* out);
+ppsp_status ppsp_potential_eval(ppsp_graph* g, uint32_t anchor, const uint32_t* vertices,
+                                uint64_t count, int64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPSP_H */

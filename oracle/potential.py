@@ -10,13 +10,13 @@ library uses a scaled, fixed-point form whose consistency is certified edge by
 edge:
 
 * the graph's scale c (float64) is chosen at graph creation;
-* integer potential coordinates P(v) = floor(16 * c * p(v) + 0.5), computed per
-  component in float64 from the float32 input coordinates p(v) as
-  ``floor(float64(p) * (16.0 * c) + 0.5)``;
-* h_x(v) = floor(|P(v) - P(x)| / 16) = isqrt(floor((dX^2 + dY^2) / 256)), exact
-  in integers (floor(sqrt(floor(y))) = floor(sqrt(y)) for y >= 0);
-* certificate: dX^2 + dY^2 <= (16 * w)^2 on every edge (u, v).  Then
-  h_x(u) - h_x(v) <= ceil(|P(u) - P(v)| / 16) <= w(u, v), i.e. h_x is
+* a fixed-point shift F (default 4) and integer potential coordinates
+  P(v) = floor(2^F * c * p(v) + 0.5), computed per component in float64 from
+  the float32 input coordinates p(v) as ``floor(float64(p) * (2^F * c) + 0.5)``;
+* h_x(v) = floor(|P(v) - P(x)| / 2^F) = isqrt(floor((dX^2 + dY^2) / 4^F)),
+  exact in integers (floor(sqrt(floor(y))) = floor(sqrt(y)) for y >= 0);
+* certificate: dX^2 + dY^2 <= (2^F * w)^2 on every edge (u, v).  Then
+  h_x(u) - h_x(v) <= ceil(|P(u) - P(v)| / 2^F) <= w(u, v), i.e. h_x is
   consistent for every anchor x, and h_x(x) = 0.
 """
 
@@ -27,18 +27,18 @@ import math
 import numpy as np
 
 
-def potential_coords(coords: np.ndarray, c: float) -> np.ndarray:
-    """P(v) = floor(float64(p(v)) * (16 c) + 0.5) as int64 [n, 2]."""
-    s = np.float64(16.0) * np.float64(c)
+def potential_coords(coords: np.ndarray, c: float, shift: int = 4) -> np.ndarray:
+    """P(v) = floor(float64(p(v)) * (2^F c) + 0.5) as int64 [n, 2]."""
+    s = np.float64(1 << shift) * np.float64(c)
     p = np.asarray(coords, dtype=np.float32).astype(np.float64)
     return np.floor(p * s + 0.5).astype(np.int64)
 
 
-def h_one(P: np.ndarray, x: int, v: int) -> int:
+def h_one(P: np.ndarray, x: int, v: int, shift: int = 4) -> int:
     """h_x(v) with Python integers and math.isqrt (the definition)."""
     dx = int(P[v, 0]) - int(P[x, 0])
     dy = int(P[v, 1]) - int(P[x, 1])
-    return math.isqrt((dx * dx + dy * dy) >> 8)
+    return math.isqrt((dx * dx + dy * dy) >> (2 * shift))
 
 
 def isqrt_array(d: np.ndarray) -> np.ndarray:
@@ -54,19 +54,20 @@ def isqrt_array(d: np.ndarray) -> np.ndarray:
     return r
 
 
-def h_all(P: np.ndarray, x: int) -> np.ndarray:
+def h_all(P: np.ndarray, x: int, shift: int = 4) -> np.ndarray:
     """h_x(v) for every v (int64 [n])."""
     d = P - P[x][None, :]
-    return isqrt_array((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) >> 8)
+    return isqrt_array((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) >> (2 * shift))
 
 
-def certificate_ok(off: np.ndarray, tgt: np.ndarray, w: np.ndarray, P: np.ndarray) -> np.ndarray:
-    """Per-edge certificate dX^2 + dY^2 <= (16 w)^2 (bool [m])."""
+def certificate_ok(off: np.ndarray, tgt: np.ndarray, w: np.ndarray, P: np.ndarray,
+                   shift: int = 4) -> np.ndarray:
+    """Per-edge certificate dX^2 + dY^2 <= (2^F w)^2 (bool [m])."""
     n = off.shape[0] - 1
     src = np.repeat(np.arange(n, dtype=np.int64), np.diff(off).astype(np.int64))
     d = P[src] - P[tgt.astype(np.int64)]
     lhs = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]
-    rhs = (16 * w.astype(np.int64)) ** 2
+    rhs = ((1 << shift) * w.astype(np.int64)) ** 2
     return lhs <= rhs
 
 

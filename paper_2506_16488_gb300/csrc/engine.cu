@@ -1,0 +1,773 @@
+// Persistent PPSP search engine for sm_103a.
+//
+// One cooperative launch runs every group of a batch.  Each team of CTAs loops:
+// claim a group, Init (Table 2), then steps of Alg. 2 until the frontier is
+// empty, then tidy its slot.  A step is
+//   theta <- GetDist(F)            Delta*-stepping threshold (Sec. 2), empty
+//                                  buckets skipped
+//   for <u,i> in F.Extract(theta)  keys <= theta; the rest stay in F
+//     UpdateDistance(<u,i>)        (see "correctness of mu" below)
+//     if not Prune(<u,i>):
+//       for v in N(u): if WriteMin(delta_i[v], delta_i[u] + w(u,v)):
+//         UpdateDistance(<v,i>); if not Prune(<v,i>): F.Add(<v,i>)
+// with one team barrier per step.  The frontier of the next step is a bitmap
+// over flat (vertex, search) indices (dedup: an entry is added once), plus a
+// queue of the newly set indices while the frontier is small ("sparse"); a
+// large frontier is processed by scanning the bitmap ("dense"), App. B.
+//
+// Keys and prune values per plug-in (Table 2), with integer arithmetic:
+//   BiDS        key = 2 d,                       prune 2 d >= mu   (mu/2 test doubled)
+//   BiD-A*      key = 2 d + rho_i(v) - rho_i(q_i), prune 2 d + rho_i(v) >= mu,
+//               rho_i(v) = h_{q_j}(v) - h_{q_i}(v)  (= 2 h_F for the forward search,
+//               2 h_B for the backward one: h_F = (h_t - h_s)/2 = -h_B, Sec. 4.5)
+//   Multi-BiDS  key = 2 d,                       prune 2 d >= mumax[i]  (Sec. 5.2)
+//   ET          key = d,                         prune d >= mu, update when v = t
+//   A*          key = d + h_t(v) - h_t(s),       prune d + h_t(v) >= mu
+// The threshold step is 2 Delta on doubled keys and Delta otherwise.
+//
+// Correctness of mu.  Theorems 4.1/4.2 need, for the two ends x of some edge on
+// a shortest path, that mu is updated after both delta_i[x] and delta_j[x] hold
+// their final values.  The update at a successful WriteMin reads the other
+// search's value; when the two final writes race inside one step neither reader
+// may see the other's write.  The extraction-time update closes that gap: steps
+// are separated by a barrier with device-scope fences, and if both copies were
+// pruned on insertion then 2(delta_i + delta_j) >= mu_i + mu_j >= 2 mu, so x
+// cannot improve mu; otherwise one copy is extracted in a later step and its
+// update reads both final values.
+#include <cooperative_groups.h>
+
+#include "ppsp_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace ppsp {
+
+// ----------------------------------------------------------------------------
+// device helpers
+// ----------------------------------------------------------------------------
+template <typename D>
+struct DT;
+template <>
+struct DT<u32> {
+    static constexpr u64 INF = 0xFFFFFFFFull;
+    static constexpr u64 MAXV = 0xFFFFFFFEull;
+};
+template <>
+struct DT<u64> {
+    static constexpr u64 INF = ~0ull;
+    static constexpr u64 MAXV = (1ull << 61);
+};
+
+__device__ __forceinline__ u64 ld_dist(const u32* p) { return (u64)__ldcg(p); }
+__device__ __forceinline__ u64 ld_dist(const u64* p) {
+    return (u64)__ldcg(reinterpret_cast<const unsigned long long*>(p));
+}
+__device__ __forceinline__ u64 amin_dist(u32* p, u64 v) { return (u64)atomicMin(p, (u32)v); }
+__device__ __forceinline__ u64 amin_dist(u64* p, u64 v) {
+    return (u64)atomicMin(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+__device__ __forceinline__ void st_dist(u32* p, u64 v) { *p = (u32)v; }
+__device__ __forceinline__ void st_dist(u64* p, u64 v) { *p = v; }
+
+__device__ __forceinline__ u64 ldcg64(const u64* p) {
+    return (u64)__ldcg(reinterpret_cast<const unsigned long long*>(p));
+}
+__device__ __forceinline__ u64 amin64(u64* p, u64 v) {
+    return (u64)atomicMin(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+__device__ __forceinline__ u32 ld_volatile(const u32* p) { return *reinterpret_cast<const volatile u32*>(p); }
+
+// Exact floor(sqrt(x)) for x < 2^62: float64 estimate, then integer correction.
+__device__ __forceinline__ u64 isqrt_u64(u64 x) {
+    u64 r = (u64)sqrt((double)x);
+    while (r * r > x) --r;
+    while ((r + 1) * (r + 1) <= x) ++r;
+    return r;
+}
+
+// h_x(v) = floor(|P(v) - P(x)| / 2^F)  (integer potential, Sec. 4.3).
+__device__ __forceinline__ i64 pot_h(int2 px, int2 pv, u32 shift) {
+    i64 dx = (i64)pv.x - (i64)px.x;
+    i64 dy = (i64)pv.y - (i64)px.y;
+    u64 d2 = (u64)(dx * dx) + (u64)(dy * dy);
+    return (i64)isqrt_u64(d2 >> (2 * shift));
+}
+
+__device__ __forceinline__ u32 agg_inc(u32* ctr) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    u32 base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(ctr, (u32)g.size());
+    base = g.shfl(base, 0);
+    return base + g.thread_rank();
+}
+
+// ----------------------------------------------------------------------------
+// team barrier: bounded spin, device-scope release/acquire
+// ----------------------------------------------------------------------------
+struct TeamCtx {
+    u32 team, rank, size;
+    TeamState* ts;
+    bool global_bar;  // size > 1 or a test hook forces the global path
+    u32 expect;       // arrivals that release the barrier
+};
+
+__device__ bool team_sync(const TeamCtx& tc, const EngineArgs& a, u32* s_flag) {
+    __syncthreads();
+    if (!tc.global_bar) return true;
+    if (threadIdx.x == 0) {
+        u32 ok = 1;
+        u32 gen = ld_volatile(&tc.ts->bar_gen);
+        __threadfence();
+        u32 arrived = atomicAdd(&tc.ts->bar_count, 1u);
+        if (arrived == tc.expect - 1) {
+            tc.ts->bar_count = 0;
+            __threadfence();
+            atomicAdd(&tc.ts->bar_gen, 1u);
+        } else {
+            u64 it = 0;
+            while (ld_volatile(&tc.ts->bar_gen) == gen) {
+                if (++it > a.spin_limit || ld_volatile(a.err) != 0) {
+                    atomicOr(a.err, ERRB_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+// ----------------------------------------------------------------------------
+// shared memory
+// ----------------------------------------------------------------------------
+template <int B>
+struct Smem {
+    // tile of frontier entries
+    u32 flat[B];
+    u32 v[B];
+    u32 beg[B];
+    u32 pre[B];
+    u64 d[B];
+    unsigned char si[B];
+    u32 wsum[B / 32];
+    // group cache
+    u32 src[KMAX];
+    u32 pbeg[KMAX];
+    u32 pcnt[KMAX];
+    u32 pot[KMAX];
+    int2 pa[KMAX];
+    int2 pb[KMAX];
+    i64 key_off[KMAX];
+    u64 bound[KMAX];
+    // step scalars
+    u64 minkey;
+    u32 count, overflow, dir0, dir1, tile, flag, total, nitems;
+    u32 cnt_dir[2];
+    u32 group;
+    u64 mu0;
+};
+
+template <int B>
+__device__ __forceinline__ u32 block_excl_scan(u32 x, Smem<B>& sm, u32* total) {
+    const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    u32 incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (u32)o) incl += y;
+    }
+    if (lane == 31) sm.wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        u32 s = (lane < B / 32) ? sm.wsum[lane] : 0;
+        u32 si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            u32 y = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= (u32)o) si += y;
+        }
+        if (lane < B / 32) sm.wsum[lane] = si - s;  // exclusive warp offsets
+        if (lane == B / 32 - 1) sm.total = si;
+    }
+    __syncthreads();
+    *total = sm.total;
+    return sm.wsum[wid] + incl - x;
+}
+
+// ----------------------------------------------------------------------------
+// per-group context
+// ----------------------------------------------------------------------------
+template <typename D>
+struct GCtx {
+    GroupDev G;
+    D* dist;
+    u32* bm_cur;
+    u32* bm_nxt;
+    u32* q_nxt;
+    StepState* S_nxt;
+    SlotDev slot;
+    u64 theta;
+    bool dense_nxt;
+    u32 n;
+    // per-thread counters
+    u64 c_x, c_e, c_r, c_p, c_t;
+};
+
+__device__ __forceinline__ u32 flat_of(const GroupDev& G, u32 n, u32 v, u32 i) {
+    return G.layout == PPSP_LAYOUT_INTERLEAVED ? ((v << G.kshift) | i) : (i * n + v);
+}
+__device__ __forceinline__ void decode_flat(const GroupDev& G, u32 n, u32 f, u32& v, u32& i) {
+    if (G.layout == PPSP_LAYOUT_INTERLEAVED) {
+        v = f >> G.kshift;
+        i = f & ((1u << G.kshift) - 1u);
+    } else {
+        i = f / n;
+        v = f - i * n;
+    }
+}
+
+// key and prune value of <v, i> at tentative distance d
+template <int B>
+__device__ __forceinline__ void key_pv(const EngineArgs& a, const GroupDev& G, const Smem<B>& sm,
+                                       u32 i, u32 v, u64 d, i64& key, i64& pv) {
+    if (G.mode == GM_BIDIR) {
+        i64 rho = 0;
+        if (sm.pot[i]) {
+            int2 pv2 = a.g.pc[v];
+            rho = pot_h(sm.pb[i], pv2, a.g.pot_shift) - pot_h(sm.pa[i], pv2, a.g.pot_shift);
+        }
+        pv = 2 * (i64)d + rho;
+        key = pv + sm.key_off[i];
+    } else if (G.mode == GM_ASTAR) {
+        i64 ht = pot_h(sm.pb[0], a.g.pc[v], a.g.pot_shift);
+        pv = (i64)d + ht;
+        key = pv + sm.key_off[0];
+    } else {
+        pv = (i64)d;
+        key = (i64)d;
+    }
+    if (key < 0) key = 0;
+}
+
+__device__ __forceinline__ bool pruned(i64 pv, u64 bound) {
+    return bound != INF64 && pv >= 0 && (u64)pv >= bound;
+}
+
+// mu[qe] <- min(mu[qe], s); on improvement refresh mumax of both ends (Table 2,
+// Multi-PPSP: WriteMin(mumax[i], max_j mu[<q_i, q_j>])).
+template <int B>
+__device__ __forceinline__ void try_mu(const EngineArgs& a, const GroupDev& G, const Smem<B>& sm,
+                                       u32 qe, u64 s) {
+    if (s >= ldcg64(a.mu + qe)) return;
+    u64 old = amin64(a.mu + qe, s);
+    if (s >= old || G.qcnt <= 1 || G.mode != GM_BIDIR) return;
+    QEdgeDev e = a.qedges[qe];
+    u32 ends[2] = {e.a, e.b};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        u32 x = ends[k];
+        u64 m = 0;
+        for (u32 p = 0; p < sm.pcnt[x]; ++p) {
+            u64 mv = ldcg64(a.mu + a.partners[sm.pbeg[x] + p].qe);
+            m = mv > m ? mv : m;
+        }
+        amin64(a.mumax + G.sbeg + x, m);
+    }
+}
+
+// UpdateDistance for <v, i> at distance d (bidirectional family)
+template <typename D, int B>
+__device__ __forceinline__ void update_bidir(const EngineArgs& a, GCtx<D>& c, const Smem<B>& sm,
+                                             u32 v, u32 i, u64 d) {
+    const u32 pb = sm.pbeg[i], pc = sm.pcnt[i];
+    for (u32 p = 0; p < pc; ++p) {
+        PartnerDev pd = a.partners[pb + p];
+        u64 o = ld_dist(c.dist + flat_of(c.G, c.n, v, pd.j));
+        if (o != DT<D>::INF) try_mu(a, c.G, sm, pd.qe, d + o);
+    }
+}
+
+template <typename D, int B>
+__device__ __forceinline__ void insert(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 f, u32 i,
+                                       i64 key) {
+    const u32 bit = 1u << (f & 31u);
+    u32 old = atomicOr(c.bm_nxt + (f >> 5), bit);
+    if (!(old & bit)) {
+        ++c.c_p;
+        if (c.G.scnt == 2) atomicAdd(&sm.cnt_dir[i], 1u);
+        u32 pos = agg_inc(&c.S_nxt->count);
+        if (!c.dense_nxt) {
+            if (pos < c.slot.qcap)
+                c.q_nxt[pos] = f;
+            else
+                c.S_nxt->overflow = 1u;
+        }
+    }
+    atomicMin(reinterpret_cast<unsigned long long*>(&sm.minkey), (unsigned long long)key);
+}
+
+template <typename D, int B>
+__device__ __forceinline__ void relax(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 i, u64 d,
+                                      uint2 ew) {
+    const u32 v2 = ew.x;
+    const u64 nd = d + (u64)ew.y;
+    if (nd > DT<D>::MAXV) {
+        atomicOr(a.err, ERRB_OVERFLOW);
+        return;
+    }
+    const u32 f2 = flat_of(c.G, c.n, v2, i);
+    if (nd >= ld_dist(c.dist + f2)) return;
+    u64 old = amin_dist(c.dist + f2, nd);
+    if (nd >= old) return;
+    ++c.c_r;
+    if (old == DT<D>::INF) {
+        ++c.c_t;
+        u32 pos = agg_inc(&c.slot.st->touched_n);
+        if (pos < c.slot.tcap)
+            c.slot.touched[pos] = f2;
+        else
+            c.slot.st->touched_overflow = 1u;
+    }
+    if (c.G.mode == GM_BIDIR) {
+        update_bidir<D, B>(a, c, sm, v2, i, nd);
+    } else if (c.G.mode != GM_SSSP && v2 == c.G.target) {
+        try_mu(a, c.G, sm, c.G.qbeg, nd);
+    }
+    i64 key, pv;
+    key_pv<B>(a, c.G, sm, i, v2, nd, key, pv);
+    if (pruned(pv, sm.bound[i])) return;
+    insert<D, B>(a, c, sm, f2, i, key);
+}
+
+// Process sm.flat[0 .. cnt): extract, update, prune, then relax all edges of
+// the survivors with a load-balanced sweep (consecutive threads read
+// consecutive adjacency entries).
+template <typename D, int B>
+__device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 cnt, bool sparse_src,
+                              u32* bm_cur) {
+    const u32 t = threadIdx.x;
+    // refresh prune bounds for this tile
+    if (t < c.G.scnt) {
+        u64 b;
+        if (c.G.mode == GM_BIDIR)
+            b = (c.G.qcnt == 1) ? ldcg64(a.mu + c.G.qbeg) : ldcg64(a.mumax + c.G.sbeg + t);
+        else if (c.G.mode == GM_SSSP)
+            b = INF64;
+        else
+            b = ldcg64(a.mu + c.G.qbeg);
+        sm.bound[t] = b;
+    }
+    __syncthreads();
+    u32 deg = 0;
+    if (t < cnt) {
+        const u32 f = sm.flat[t];
+        u32 v, i;
+        decode_flat(c.G, c.n, f, v, i);
+        if (sparse_src) atomicAnd(bm_cur + (f >> 5), ~(1u << (f & 31u)));
+        const u64 d = ld_dist(c.dist + f);
+        if (d != DT<D>::INF) {
+            i64 key, pv;
+            key_pv<B>(a, c.G, sm, i, v, d, key, pv);
+            if ((u64)key > c.theta) {
+                insert<D, B>(a, c, sm, f, i, key);  // stays in F
+            } else {
+                if (c.G.mode == GM_BIDIR) update_bidir<D, B>(a, c, sm, v, i, d);
+                if (!pruned(pv, sm.bound[i])) {
+                    const u32 b0 = __ldg(a.g.off + v);
+                    deg = __ldg(a.g.off + v + 1) - b0;
+                    sm.beg[t] = b0;
+                    sm.v[t] = v;
+                    sm.si[t] = (unsigned char)i;
+                    sm.d[t] = d;
+                    ++c.c_x;
+                }
+            }
+        }
+    }
+    u32 total;
+    u32 excl = block_excl_scan<B>(deg, sm, &total);
+    sm.pre[t] = (t < cnt) ? excl : total;
+    __syncthreads();
+    c.c_e += 0;
+    for (u32 e = t; e < total; e += B) {
+        u32 lo = 0, hi = cnt;
+        while (hi - lo > 1) {
+            u32 mid = (lo + hi) >> 1;
+            if (sm.pre[mid] <= e) lo = mid; else hi = mid;
+        }
+        const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
+        const uint2 ew = __ldg(a.g.edges + edge);
+        ++c.c_e;
+        relax<D, B>(a, c, sm, sm.si[lo], sm.d[lo], ew);
+    }
+    __syncthreads();
+}
+
+// ----------------------------------------------------------------------------
+// one group
+// ----------------------------------------------------------------------------
+template <typename D, int B>
+__device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev& slot, u32 gi,
+                          Smem<B>& sm, u64* cnt_acc) {
+    const u32 t = threadIdx.x;
+    GCtx<D> c;
+    c.G = a.groups[gi];
+    c.slot = slot;
+    c.dist = reinterpret_cast<D*>(slot.dist);
+    c.n = a.g.n;
+    c.c_x = c.c_e = c.c_r = c.c_p = c.c_t = 0;
+    const GroupDev& G = c.G;
+    StepState* S = slot.st->s;
+
+    // group cache
+    if (t < G.scnt) {
+        SearchDev s = a.searches[G.sbeg + t];
+        sm.src[t] = s.src;
+        sm.pbeg[t] = s.pbeg;
+        sm.pcnt[t] = s.pcnt;
+        sm.pot[t] = s.pot;
+        sm.key_off[t] = s.key_off;
+        if (a.g.pc != nullptr) {
+            sm.pa[t] = a.g.pc[s.src];
+            sm.pb[t] = a.g.pc[s.pot_b];
+        }
+    }
+    __syncthreads();
+
+    // Init (Table 2): delta_i[q_i] = 0 and <q_i, i> in F for every search;
+    // mu = inf (0 when both ends coincide).
+    if (tc.rank == 0) {
+        if (t < G.scnt) {
+            const u32 f = flat_of(G, c.n, sm.src[t], t);
+            st_dist(c.dist + f, 0);
+            atomicOr(slot.bm[0] + (f >> 5), 1u << (f & 31u));
+            slot.q[0][t] = f;
+            slot.touched[t] = f;
+        }
+        if (t < G.qcnt) {
+            QEdgeDev e = a.qedges[G.qbeg + t];
+            u64 m;
+            if (G.mode == GM_BIDIR)
+                m = (sm.src[e.a] == sm.src[e.b]) ? 0 : INF64;
+            else if (G.mode == GM_SSSP)
+                m = INF64;
+            else
+                m = (sm.src[0] == G.target) ? 0 : INF64;
+            a.mu[G.qbeg + t] = m;
+        }
+        if (t == 0) {
+            S[0].count = G.scnt;
+            S[0].minkey = 0;
+            S[0].tile = 0;
+            S[0].overflow = 0;
+            S[0].cnt_dir[0] = 1;
+            S[0].cnt_dir[1] = G.scnt == 2 ? 1 : 0;
+            S[1].count = 0;
+            S[1].minkey = INF64;
+            S[1].tile = 0;
+            S[1].overflow = 0;
+            S[1].cnt_dir[0] = S[1].cnt_dir[1] = 0;
+            slot.st->touched_n = G.scnt;
+            slot.st->touched_overflow = 0;
+        }
+        __syncthreads();
+        if (t < G.scnt && G.mode == GM_BIDIR) {
+            u64 m = 0;
+            for (u32 p = 0; p < sm.pcnt[t]; ++p) {
+                u64 mv = a.mu[a.partners[sm.pbeg[t] + p].qe];
+                m = mv > m ? mv : m;
+            }
+            a.mumax[G.sbeg + t] = (sm.pcnt[t] == 0) ? INF64 : m;
+        }
+    }
+    if (!team_sync(tc, a, &sm.flag)) return false;
+
+    const u64 step = (G.mode == GM_BIDIR) ? 2 * G.delta : G.delta;
+    const u32 flat_range = (G.layout == PPSP_LAYOUT_INTERLEAVED) ? (c.n << G.kshift) : G.scnt * c.n;
+    const u32 nwords = (flat_range + 31u) >> 5;
+    u64 dense_thresh = (a.dense_den == 0) ? ~0ull : (u64)flat_range / a.dense_den;
+    c.theta = 0;
+    bool dense_cur = (a.frontier == PPSP_FRONTIER_DENSE);
+    u32 r = 0;
+    u64 rounds = 0, dense_rounds = 0;
+    u32 exit_count = 0, exit_bcur = 0;
+    bool exit_dense = false;
+    for (;; ++r) {
+        const u32 cur = r % 3, nxt = (r + 1) % 3, old = (r + 2) % 3;
+        const u32 bcur = r & 1u, bnxt = bcur ^ 1u;
+        if (t == 0) {
+            sm.count = ld_volatile(&S[cur].count);
+            sm.overflow = ld_volatile(&S[cur].overflow);
+            sm.minkey = ldcg64(&S[cur].minkey);
+            sm.dir0 = ld_volatile(&S[cur].cnt_dir[0]);
+            sm.dir1 = ld_volatile(&S[cur].cnt_dir[1]);
+            sm.mu0 = ldcg64(a.mu + G.qbeg);
+        }
+        __syncthreads();
+        const u32 count = sm.count;
+        const u64 minkey = sm.minkey;
+        dense_cur = dense_cur || sm.overflow != 0;
+        bool stop = (count == 0);
+        // App. B: a two-search group whose one side ran dry before mu was ever
+        // set is disconnected.
+        if (!stop && G.mode == GM_BIDIR && G.scnt == 2 && sm.mu0 == INF64 &&
+            (sm.dir0 == 0 || sm.dir1 == 0))
+            stop = true;
+        if (stop) {
+            exit_count = count;
+            exit_bcur = bcur;
+            exit_dense = dense_cur;
+            break;
+        }
+        // GetDist: next multiple of the step, at least one step further and
+        // not below the smallest key in F.
+        {
+            u64 want = c.theta + step;
+            u64 rk = (minkey / step) * step;
+            if (rk < minkey) rk += step;
+            c.theta = want > rk ? want : rk;
+        }
+        c.dense_nxt = (a.frontier == PPSP_FRONTIER_DENSE) ||
+                      (a.frontier == PPSP_FRONTIER_AUTO && (u64)count > dense_thresh);
+        c.bm_cur = slot.bm[bcur];
+        c.bm_nxt = slot.bm[bnxt];
+        c.q_nxt = slot.q[bnxt];
+        c.S_nxt = &S[nxt];
+        if (tc.rank == 0 && t == 0) {
+            S[old].count = 0;
+            S[old].minkey = INF64;
+            S[old].tile = 0;
+            S[old].overflow = 0;
+            S[old].cnt_dir[0] = S[old].cnt_dir[1] = 0;
+        }
+        if (t == 0) {
+            sm.minkey = INF64;
+            sm.cnt_dir[0] = sm.cnt_dir[1] = 0;
+        }
+        __syncthreads();
+        ++rounds;
+        if (dense_cur) ++dense_rounds;
+
+        if (!dense_cur) {
+            const u32 nt = (count + B - 1) / B;
+            u32 local = tc.rank;
+            for (;;) {
+                if (t == 0) sm.tile = tc.size == 1 ? local : atomicAdd(&S[cur].tile, 1u);
+                __syncthreads();
+                const u32 tile = sm.tile;
+                __syncthreads();
+                if (tile >= nt) break;
+                local += tc.size;
+                const u32 base = tile * B;
+                const u32 cnt = min((u32)B, count - base);
+                if (t < cnt) sm.flat[t] = __ldcg(slot.q[bcur] + base + t);
+                __syncthreads();
+                process_items<D, B>(a, c, sm, cnt, true, c.bm_cur);
+            }
+        } else {
+            const u32 nt = (nwords + B - 1) / B;
+            u32 local = tc.rank;
+            for (;;) {
+                if (t == 0) sm.tile = tc.size == 1 ? local : atomicAdd(&S[cur].tile, 1u);
+                __syncthreads();
+                const u32 tile = sm.tile;
+                __syncthreads();
+                if (tile >= nt) break;
+                local += tc.size;
+                const u32 w = tile * B + t;
+                u32 bits = 0;
+                if (w < nwords) {
+                    bits = __ldcg(c.bm_cur + w);
+                    if (bits) c.bm_cur[w] = 0u;
+                }
+                u32 total;
+                u32 idx = block_excl_scan<B>(__popc(bits), sm, &total);
+                for (u32 base = 0; base < total; base += B) {
+                    while (bits && idx < base + B) {
+                        const u32 b = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        sm.flat[idx - base] = (w << 5) | b;
+                        ++idx;
+                    }
+                    __syncthreads();
+                    process_items<D, B>(a, c, sm, min((u32)B, total - base), false, c.bm_cur);
+                }
+            }
+        }
+        // flush per-CTA step results
+        __syncthreads();
+        if (t == 0) {
+            if (sm.minkey != INF64)
+                amin64(&S[nxt].minkey, sm.minkey);
+            if (sm.cnt_dir[0]) atomicAdd(&S[nxt].cnt_dir[0], sm.cnt_dir[0]);
+            if (sm.cnt_dir[1]) atomicAdd(&S[nxt].cnt_dir[1], sm.cnt_dir[1]);
+        }
+        if (!team_sync(tc, a, &sm.flag)) return false;
+        dense_cur = c.dense_nxt;
+    }
+
+    // ---- tidy the slot ----
+    if (exit_count > 0) {
+        // the frontier was abandoned (disconnected exit): clear its bits
+        u32* bm = slot.bm[exit_bcur];
+        if (exit_dense) {
+            for (u32 w = tc.rank * B + t; w < nwords; w += tc.size * B) bm[w] = 0u;
+        } else {
+            const u32 q_n = min(exit_count, slot.qcap);
+            for (u32 k = tc.rank * B + t; k < q_n; k += tc.size * B) bm[__ldcg(slot.q[exit_bcur] + k) >> 5] = 0u;
+        }
+    }
+    {
+        const u32 tn = ld_volatile(&slot.st->touched_n);
+        const u32 tov = ld_volatile(&slot.st->touched_overflow);
+        if (tov) {
+            for (u32 f = tc.rank * B + t; f < flat_range; f += tc.size * B) st_dist(c.dist + f, DT<D>::INF);
+        } else {
+            for (u32 k = tc.rank * B + t; k < tn; k += tc.size * B)
+                st_dist(c.dist + __ldcg(slot.touched + k), DT<D>::INF);
+        }
+    }
+    cnt_acc[0] += c.c_x;
+    cnt_acc[1] += c.c_e;
+    cnt_acc[2] += c.c_r;
+    cnt_acc[3] += c.c_p;
+    cnt_acc[4] += c.c_t;
+    if (t == 0 && tc.rank == 0) {
+        cnt_acc[5] += rounds;
+        cnt_acc[6] += 1;
+        cnt_acc[7] += G.scnt;
+        cnt_acc[8] += dense_rounds;
+    }
+    return team_sync(tc, a, &sm.flag);
+}
+
+template <typename D, int B>
+__global__ void __launch_bounds__(B) engine_kernel(EngineArgs a) {
+    __shared__ Smem<B> sm;
+    TeamCtx tc;
+    tc.team = a.cta_team[blockIdx.x];
+    tc.rank = blockIdx.x - a.team_first[tc.team];
+    tc.size = a.team_size[tc.team];
+    tc.ts = a.tstate + tc.team;
+    const bool never = (a.debug & PPSP_DEBUG_BARRIER_NEVER_RELEASES) != 0;
+    tc.global_bar = tc.size > 1 || never;
+    tc.expect = tc.size + (never ? 1u : 0u);
+    const u32 qid = a.team_queue[tc.team];
+    const SlotDev slot = a.slots[tc.team];
+    u64 acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            if (tc.rank == 0) {
+                u32 idx = atomicAdd(a.queue_head + qid, 1u);
+                u32 g = idx < a.queue_len[qid] ? a.queue_items[qid][idx] : NONE;
+                if (tc.global_bar) tc.ts->group = g;
+                sm.group = g;
+            }
+        }
+        if (!team_sync(tc, a, &sm.flag)) break;
+        if (tc.global_bar && threadIdx.x == 0) sm.group = ld_volatile(&tc.ts->group);
+        __syncthreads();
+        const u32 gi = sm.group;
+        if (!team_sync(tc, a, &sm.flag)) break;  // everyone has read ts->group
+        if (gi == NONE) break;
+        if (!run_group<D, B>(a, tc, slot, gi, sm, acc)) break;
+    }
+    // counters
+    if (a.counters) {
+        unsigned long long* cp = &a.counters->extracted;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            u64 x = acc[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) == 0 && x) atomicAdd(cp + k, (unsigned long long)x);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// host side
+// ----------------------------------------------------------------------------
+template <typename D, int B>
+static ppsp_status launch_t(const EngineArgs& a, u32 grid, cudaStream_t stream) {
+    EngineArgs args = a;
+    void* params[] = {&args};
+    PPSP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)engine_kernel<D, B>, dim3(grid), dim3(B),
+                                              params, 0, stream));
+    return PPSP_OK;
+}
+
+ppsp_status launch_engine(const EngineArgs& a, int dist_bits, int block_threads, u32 grid,
+                          cudaStream_t stream) {
+    if (dist_bits == 32) {
+        if (block_threads == 256) return launch_t<u32, 256>(a, grid, stream);
+        if (block_threads == 512) return launch_t<u32, 512>(a, grid, stream);
+        if (block_threads == 1024) return launch_t<u32, 1024>(a, grid, stream);
+    } else {
+        if (block_threads == 256) return launch_t<u64, 256>(a, grid, stream);
+        if (block_threads == 512) return launch_t<u64, 512>(a, grid, stream);
+        if (block_threads == 1024) return launch_t<u64, 1024>(a, grid, stream);
+    }
+    return PPSP_ERR_INVALID_ARG;
+}
+
+template <typename D, int B>
+static ppsp_status occ_t(int* bpsm) {
+    PPSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bpsm, engine_kernel<D, B>, B, 0));
+    return PPSP_OK;
+}
+
+ppsp_status engine_occupancy(int dist_bits, int block_threads, int* blocks_per_sm, int* sms) {
+    int dev = 0;
+    PPSP_CUDA_TRY(cudaGetDevice(&dev));
+    PPSP_CUDA_TRY(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev));
+    if (dist_bits == 32) {
+        if (block_threads == 256) return occ_t<u32, 256>(blocks_per_sm);
+        if (block_threads == 512) return occ_t<u32, 512>(blocks_per_sm);
+        if (block_threads == 1024) return occ_t<u32, 1024>(blocks_per_sm);
+    } else {
+        if (block_threads == 256) return occ_t<u64, 256>(blocks_per_sm);
+        if (block_threads == 512) return occ_t<u64, 512>(blocks_per_sm);
+        if (block_threads == 1024) return occ_t<u64, 1024>(blocks_per_sm);
+    }
+    return PPSP_ERR_INVALID_ARG;
+}
+
+// ---- potential evaluation (for checks against the oracle) ----
+__global__ void potential_eval_kernel(GraphDev g, u32 anchor, const u32* verts, u64 count, i64* out) {
+    u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    u32 v = verts[k];
+    out[k] = (v < g.n) ? pot_h(g.pc[anchor], g.pc[v], g.pot_shift) : -1;
+}
+
+ppsp_status launch_potential_eval(const GraphDev& g, u32 anchor, const u32* d_verts, u64 count,
+                                  i64* d_out, cudaStream_t stream) {
+    if (count == 0) return PPSP_OK;
+    u32 blocks = (u32)((count + 255) / 256);
+    potential_eval_kernel<<<blocks, 256, 0, stream>>>(g, anchor, d_verts, count, d_out);
+    PPSP_CUDA_TRY(cudaGetLastError());
+    return PPSP_OK;
+}
+
+__global__ void scatter_kernel(const u32* map, const u64* mu, u64 k, u64* out) {
+    u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= k) return;
+    u32 m = map[q];
+    out[q] = (m == NONE) ? 0ull : mu[m];
+}
+
+ppsp_status launch_scatter(const u32* d_map, const u64* d_mu, u64 k, u64* d_out, cudaStream_t s) {
+    if (k == 0) return PPSP_OK;
+    u32 blocks = (u32)((k + 255) / 256);
+    scatter_kernel<<<blocks, 256, 0, s>>>(d_map, d_mu, k, d_out);
+    PPSP_CUDA_TRY(cudaGetLastError());
+    return PPSP_OK;
+}
+
+}  // namespace ppsp

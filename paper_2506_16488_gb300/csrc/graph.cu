@@ -1,0 +1,399 @@
+// Graph creation, validation, A* potential, slot pool, small ABI helpers.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <thread>
+
+#include "graph_impl.h"
+
+namespace ppsp {
+
+static thread_local char g_last_error[512] = {0};
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file,
+             line);
+}
+
+u64 isqrt_host(u64 x) {
+    // bitwise integer square root: exact floor(sqrt(x))
+    u64 r = 0, bit = 1ull << 62;
+    while (bit > x) bit >>= 2;
+    while (bit != 0) {
+        if (x >= r + bit) {
+            x -= r + bit;
+            r = (r >> 1) + bit;
+        } else {
+            r >>= 1;
+        }
+        bit >>= 2;
+    }
+    return r;
+}
+
+i64 pot_h_host(const ppsp_graph* g, u32 x, u32 v) {
+    if (g->pc_host.empty()) return 0;
+    i64 dx = g->pc_host[2 * (u64)v] - g->pc_host[2 * (u64)x];
+    i64 dy = g->pc_host[2 * (u64)v + 1] - g->pc_host[2 * (u64)x + 1];
+    u64 d2 = (u64)(dx * dx) + (u64)(dy * dy);
+    return (i64)isqrt_host(d2 >> (2 * g->pot_shift));
+}
+
+template <typename F>
+static void parallel_for(u64 n, F f) {
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (n < (1u << 16)) nt = 1;
+    std::vector<std::thread> th;
+    for (unsigned k = 0; k < nt; ++k)
+        th.emplace_back([=, &f]() {
+            u64 lo = n * k / nt, hi = n * (k + 1) / nt;
+            f(lo, hi, k);
+        });
+    for (auto& t : th) t.join();
+}
+
+// The certified integer potential (Sec. 4.3, Fact 4.1): choose c and F, round
+// P(v) = floor(p(v) * c * 2^F + 0.5), and check |P(u)-P(v)|^2 <= (2^F w)^2 on
+// every edge in exact integer arithmetic; shrink c until the check passes.
+static void build_potential(ppsp_graph* g, const u64* off, const u32* tgt, const u32* w, const float* xy) {
+    const u64 n = g->n;
+    double cmax = INFINITY;
+    double amax = 0.0;
+    bool zero_block = false;
+    u64 wmin_pos = ~0ull;
+    for (u64 v = 0; v < n; ++v) {
+        amax = std::max(amax, (double)std::fabs(xy[2 * v]));
+        amax = std::max(amax, (double)std::fabs(xy[2 * v + 1]));
+    }
+    for (u64 u = 0; u < n; ++u)
+        for (u64 e = off[u]; e < off[u + 1]; ++e) {
+            u64 v = tgt[e];
+            double dx = (double)xy[2 * u] - (double)xy[2 * v];
+            double dy = (double)xy[2 * u + 1] - (double)xy[2 * v + 1];
+            double l = std::sqrt(dx * dx + dy * dy);
+            if (l > 0.0) {
+                if (w[e] == 0) zero_block = true;
+                cmax = std::min(cmax, (double)w[e] / l);
+                wmin_pos = std::min<u64>(wmin_pos, w[e]);
+            }
+        }
+    g->pc_host.assign(2 * n, 0);
+    if (zero_block || !std::isfinite(cmax) || cmax <= 0.0 || amax == 0.0) {
+        g->pot_scale = 0.0;
+        g->pot_shift = 0;
+        return;
+    }
+    int F = 8;
+    while (F > 0 && amax * cmax * std::ldexp(1.0, F) >= std::ldexp(1.0, 30)) --F;
+    if (amax * cmax * std::ldexp(1.0, F) >= std::ldexp(1.0, 30)) {
+        g->pot_scale = 0.0;
+        g->pot_shift = 0;
+        return;
+    }
+    double eps = 2.0 / (std::ldexp(1.0, F) * (double)std::max<u64>(1, wmin_pos));
+    for (int attempt = 0; attempt < 40; ++attempt, eps *= 2.0) {
+        double c = cmax * (1.0 - eps);
+        if (c <= 0.0) break;
+        const double s = std::ldexp(1.0, F) * c;
+        for (u64 v = 0; v < 2 * n; ++v) g->pc_host[v] = (int64_t)std::floor((double)xy[v] * s + 0.5);
+        std::atomic<bool> ok(true);
+        const int64_t* P = g->pc_host.data();
+        parallel_for(n, [&](u64 lo, u64 hi, unsigned) {
+            for (u64 u = lo; u < hi && ok.load(std::memory_order_relaxed); ++u)
+                for (u64 e = off[u]; e < off[u + 1]; ++e) {
+                    u64 v = tgt[e];
+                    __int128 dx = P[2 * u] - P[2 * v], dy = P[2 * u + 1] - P[2 * v + 1];
+                    __int128 lhs = dx * dx + dy * dy;
+                    __int128 rw = ((__int128)w[e]) << F;
+                    if (lhs > rw * rw) {
+                        ok = false;
+                        break;
+                    }
+                }
+        });
+        if (ok) {
+            g->pot_scale = c;
+            g->pot_shift = F;
+            return;
+        }
+    }
+    std::fill(g->pc_host.begin(), g->pc_host.end(), 0);
+    g->pot_scale = 0.0;
+    g->pot_shift = 0;
+}
+
+static bool check_symmetric(u64 n, const u64* off, const u32* tgt, const u32* w) {
+    const u64 m = off[n];
+    std::vector<u64> key(m);
+    parallel_for(n, [&](u64 lo, u64 hi, unsigned) {
+        for (u64 u = lo; u < hi; ++u) {
+            for (u64 e = off[u]; e < off[u + 1]; ++e) key[e] = ((u64)tgt[e] << 32) | w[e];
+            std::sort(key.begin() + off[u], key.begin() + off[u + 1]);
+        }
+    });
+    std::atomic<bool> ok(true);
+    parallel_for(n, [&](u64 lo, u64 hi, unsigned) {
+        for (u64 u = lo; u < hi && ok.load(std::memory_order_relaxed); ++u)
+            for (u64 e = off[u]; e < off[u + 1]; ++e) {
+                u64 v = tgt[e];
+                u64 want = (u << 32) | w[e];
+                if (!std::binary_search(key.begin() + off[v], key.begin() + off[v + 1], want)) {
+                    ok = false;
+                    break;
+                }
+            }
+    });
+    return ok;
+}
+
+ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, Slot** out) {
+    SlotKey key{dist_bits, flat_cap, qcap, tcap};
+    for (auto it = g->pool.lower_bound(key); it != g->pool.end(); ++it) {
+        Slot* s = it->second.get();
+        if (!s->busy && it->first.dist_bits == dist_bits && it->first.flat_cap >= flat_cap &&
+            it->first.qcap >= qcap && it->first.tcap >= tcap && it->first.flat_cap <= 2 * flat_cap + 4096) {
+            s->busy = true;
+            *out = s;
+            return PPSP_OK;
+        }
+    }
+    auto s = std::make_unique<Slot>();
+    const u64 W = dist_bits / 8;
+    const u64 words = (flat_cap + 31) / 32;
+    auto al = [](u64 x) { return (x + 255) & ~255ull; };
+    const u64 b_dist = al(flat_cap * W), b_bm = al(words * 4), b_q = al((u64)qcap * 4),
+              b_t = al((u64)tcap * 4), b_st = al(sizeof(SlotState));
+    s->bytes = b_dist + 2 * b_bm + 2 * b_q + b_t + b_st;
+    cudaError_t e = cudaMalloc(&s->base, s->bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? PPSP_ERR_OOM : PPSP_ERR_CUDA;
+    }
+    char* p = (char*)s->base;
+    s->dev.dist = p;
+    p += b_dist;
+    s->dev.bm[0] = (u32*)p;
+    p += b_bm;
+    s->dev.bm[1] = (u32*)p;
+    p += b_bm;
+    s->dev.q[0] = (u32*)p;
+    p += b_q;
+    s->dev.q[1] = (u32*)p;
+    p += b_q;
+    s->dev.touched = (u32*)p;
+    p += b_t;
+    s->dev.st = (SlotState*)p;
+    s->dev.flat_cap = flat_cap;
+    s->dev.qcap = qcap;
+    s->dev.tcap = tcap;
+    s->dist_bits = dist_bits;
+    s->flat_cap = flat_cap;
+    // clean invariant: distances infinite (all-ones bytes), bitmaps zero
+    PPSP_CUDA_TRY(cudaMemset(s->dev.dist, 0xFF, b_dist));
+    PPSP_CUDA_TRY(cudaMemset(s->dev.bm[0], 0, 2 * b_bm));
+    PPSP_CUDA_TRY(cudaMemset(s->dev.st, 0, b_st));
+    s->busy = true;
+    *out = s.get();
+    g->pool.emplace(key, std::move(s));
+    return PPSP_OK;
+}
+
+void slot_release(ppsp_graph* g, Slot* s) {
+    (void)g;
+    if (s) s->busy = false;
+}
+
+ppsp_status pool_scrub(ppsp_graph* g, cudaStream_t stream) {
+    if (!g->pool_dirty) return PPSP_OK;
+    for (auto& kv : g->pool) {
+        Slot* s = kv.second.get();
+        const u64 W = s->dist_bits / 8;
+        const u64 words = (s->flat_cap + 31) / 32;
+        PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.dist, 0xFF, s->flat_cap * W, stream));
+        PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.bm[0], 0, words * 4, stream));
+        PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.bm[1], 0, words * 4, stream));
+        PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.st, 0, sizeof(SlotState), stream));
+    }
+    g->pool_dirty = false;
+    return PPSP_OK;
+}
+
+}  // namespace ppsp
+
+using namespace ppsp;
+
+extern "C" {
+
+void ppsp_options_init(ppsp_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->mode = PPSP_BIDS;
+    o->dist_bits = 32;
+    o->frontier = PPSP_FRONTIER_AUTO;
+    o->layout = PPSP_LAYOUT_AUTO;
+    o->batch_strategy = PPSP_BATCH_MULTI;
+}
+
+const char* ppsp_status_string(ppsp_status s) {
+    switch (s) {
+        case PPSP_OK: return "ok";
+        case PPSP_ERR_INVALID_ARG: return "invalid argument";
+        case PPSP_ERR_BAD_GRAPH: return "malformed graph";
+        case PPSP_ERR_OOM: return "out of memory";
+        case PPSP_ERR_CUDA: return "CUDA error";
+        case PPSP_ERR_TIMEOUT: return "device wait timed out";
+        case PPSP_ERR_NO_COORDS: return "graph has no coordinates";
+        case PPSP_ERR_BUFFER_TOO_SMALL: return "buffer too small";
+        case PPSP_ERR_OVERFLOW: return "distance overflows the distance width";
+        case PPSP_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+const char* ppsp_last_error_detail(void) { return g_last_error; }
+
+ppsp_status ppsp_graph_create(uint64_t n, uint64_t m, const uint64_t* offsets, const uint32_t* targets,
+                              const uint32_t* weights, const float* coords, uint32_t flags,
+                              ppsp_graph** out) {
+    if (!out || !offsets || (m > 0 && (!targets || !weights))) return PPSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n == 0 || n >= 0xFFFFFFFFull || m >= 0xFFFFFFFFull) return PPSP_ERR_INVALID_ARG;
+    if (offsets[0] != 0 || offsets[n] != m) return PPSP_ERR_BAD_GRAPH;
+    for (u64 v = 0; v < n; ++v)
+        if (offsets[v + 1] < offsets[v]) return PPSP_ERR_BAD_GRAPH;
+    for (u64 e = 0; e < m; ++e)
+        if (targets[e] >= n) return PPSP_ERR_BAD_GRAPH;
+    if ((flags & PPSP_UNDIRECTED) && !check_symmetric(n, offsets, targets, weights)) return PPSP_ERR_BAD_GRAPH;
+
+    auto g = std::make_unique<ppsp_graph>();
+    g->n = n;
+    g->m = m;
+    ppsp_graph_info& info = g->info;
+    info.n = n;
+    info.m = m;
+    info.undirected = (flags & PPSP_UNDIRECTED) ? 1 : 0;
+    info.has_coords = coords ? 1 : 0;
+    u64 wmin = ~0ull, wmax = 0;
+    double sum = 0, sum2 = 0;
+    for (u64 e = 0; e < m; ++e) {
+        u64 x = weights[e];
+        wmin = std::min(wmin, x);
+        wmax = std::max(wmax, x);
+        sum += (double)x;
+        sum2 += (double)x * (double)x;
+        if (x == 0) info.has_zero_weight = 1;
+    }
+    info.w_min = m ? wmin : 0;
+    info.w_max = wmax;
+    info.w_mean = m ? sum / (double)m : 0.0;
+    info.w_std = m ? std::sqrt(std::max(0.0, sum2 / (double)m - info.w_mean * info.w_mean)) : 0.0;
+    g->deg.resize(n);
+    u64 dmax = 0;
+    for (u64 v = 0; v < n; ++v) {
+        g->deg[v] = offsets[v + 1] - offsets[v];
+        dmax = std::max(dmax, g->deg[v]);
+    }
+    info.deg_max = dmax;
+    if (coords) build_potential(g.get(), offsets, targets, weights, coords);
+    info.potential_scale = g->pot_scale;
+    info.potential_shift = g->pot_shift;
+
+    // device copies
+    std::vector<u32> off32(n + 1);
+    for (u64 v = 0; v <= n; ++v) off32[v] = (u32)offsets[v];
+    std::vector<uint2> ed(m);
+    for (u64 e = 0; e < m; ++e) ed[e] = make_uint2(targets[e], weights[e]);
+    cudaError_t ce;
+    if ((ce = cudaGetDevice(&g->device)) != cudaSuccess) {
+        set_last_cuda_error(ce, "cudaGetDevice", __FILE__, __LINE__);
+        cudaGetLastError();
+        return PPSP_ERR_CUDA;
+    }
+    auto fail = [&](cudaError_t e, const char* what) {
+        set_last_cuda_error(e, what, __FILE__, __LINE__);
+        cudaGetLastError();
+        cudaFree(g->d_off);
+        cudaFree(g->d_edges);
+        cudaFree(g->d_pc);
+        return e == cudaErrorMemoryAllocation ? PPSP_ERR_OOM : PPSP_ERR_CUDA;
+    };
+    if ((ce = cudaMalloc(&g->d_off, (n + 1) * 4)) != cudaSuccess) return fail(ce, "cudaMalloc(off)");
+    if ((ce = cudaMalloc(&g->d_edges, std::max<u64>(1, m) * 8)) != cudaSuccess) return fail(ce, "cudaMalloc(edges)");
+    if ((ce = cudaMemcpy(g->d_off, off32.data(), (n + 1) * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(ce, "cudaMemcpy(off)");
+    if (m && (ce = cudaMemcpy(g->d_edges, ed.data(), m * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(ce, "cudaMemcpy(edges)");
+    info.device_bytes = (n + 1) * 4 + m * 8;
+    if (coords && g->pot_scale > 0.0) {
+        std::vector<int2> pc(n);
+        for (u64 v = 0; v < n; ++v) pc[v] = make_int2((int)g->pc_host[2 * v], (int)g->pc_host[2 * v + 1]);
+        if ((ce = cudaMalloc(&g->d_pc, n * 8)) != cudaSuccess) return fail(ce, "cudaMalloc(pc)");
+        if ((ce = cudaMemcpy(g->d_pc, pc.data(), n * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(ce, "cudaMemcpy(pc)");
+        info.device_bytes += n * 8;
+    } else if (coords) {
+        // coordinates given but no positive scale exists: the potential is 0
+        std::vector<int2> pc(n, make_int2(0, 0));
+        if ((ce = cudaMalloc(&g->d_pc, n * 8)) != cudaSuccess) return fail(ce, "cudaMalloc(pc)");
+        if ((ce = cudaMemcpy(g->d_pc, pc.data(), n * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(ce, "cudaMemcpy(pc)");
+        info.device_bytes += n * 8;
+    }
+    *out = g.release();
+    return PPSP_OK;
+}
+
+void ppsp_graph_destroy(ppsp_graph* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    for (auto& kv : g->pool) cudaFree(kv.second->base);
+    g->pool.clear();
+    cudaFree(g->d_off);
+    cudaFree(g->d_edges);
+    cudaFree(g->d_pc);
+    cudaFree(g->d_scratch_u32);
+    cudaFree(g->d_scratch_i64);
+    cudaGetLastError();
+    delete g;
+}
+
+ppsp_status ppsp_graph_get_info(const ppsp_graph* g, ppsp_graph_info* out) {
+    if (!g || !out) return PPSP_ERR_INVALID_ARG;
+    *out = g->info;
+    return PPSP_OK;
+}
+
+ppsp_status ppsp_potential_coords(const ppsp_graph* g, int64_t* out) {
+    if (!g || !out) return PPSP_ERR_INVALID_ARG;
+    if (!g->info.has_coords) return PPSP_ERR_NO_COORDS;
+    memcpy(out, g->pc_host.data(), 2 * g->n * sizeof(int64_t));
+    return PPSP_OK;
+}
+
+ppsp_status ppsp_potential_eval(ppsp_graph* g, uint32_t anchor, const uint32_t* vertices, uint64_t count,
+                                int64_t* out) {
+    if (!g || (count && (!vertices || !out))) return PPSP_ERR_INVALID_ARG;
+    if (!g->info.has_coords) return PPSP_ERR_NO_COORDS;
+    if (anchor >= g->n) return PPSP_ERR_INVALID_ARG;
+    if (count == 0) return PPSP_OK;
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (count > g->scratch_cap) {
+        cudaFree(g->d_scratch_u32);
+        cudaFree(g->d_scratch_i64);
+        g->d_scratch_u32 = nullptr;
+        g->d_scratch_i64 = nullptr;
+        g->scratch_cap = 0;
+        PPSP_CUDA_TRY(cudaMalloc(&g->d_scratch_u32, count * 4));
+        PPSP_CUDA_TRY(cudaMalloc(&g->d_scratch_i64, count * 8));
+        g->scratch_cap = count;
+    }
+    PPSP_CUDA_TRY(cudaMemcpy(g->d_scratch_u32, vertices, count * 4, cudaMemcpyHostToDevice));
+    ppsp_status st = launch_potential_eval(g->dev(), anchor, g->d_scratch_u32, count, g->d_scratch_i64, 0);
+    if (st != PPSP_OK) return st;
+    PPSP_CUDA_TRY(cudaMemcpy(out, g->d_scratch_i64, count * 8, cudaMemcpyDeviceToHost));
+    return PPSP_OK;
+}
+
+}  // extern "C"

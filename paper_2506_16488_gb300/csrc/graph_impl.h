@@ -1,0 +1,80 @@
+// Host-side objects behind the opaque ppsp_graph / ppsp_plan handles.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "ppsp_internal.h"
+
+namespace ppsp {
+
+// One team's search memory (device).  Invariant between uses: every tentative
+// distance is infinity, both bitmaps are zero.
+struct Slot {
+    void* base = nullptr;   // single allocation
+    size_t bytes = 0;
+    SlotDev dev{};
+    int dist_bits = 32;
+    u64 flat_cap = 0;
+    bool busy = false;
+};
+
+struct SlotKey {
+    int dist_bits;
+    u64 flat_cap;
+    u32 qcap, tcap;
+    bool operator<(const SlotKey& o) const {
+        return std::tie(dist_bits, flat_cap, qcap, tcap) <
+               std::tie(o.dist_bits, o.flat_cap, o.qcap, o.tcap);
+    }
+};
+
+}  // namespace ppsp
+
+struct ppsp_graph {
+    int device = 0;
+    uint64_t n = 0, m = 0;
+    ppsp::u32* d_off = nullptr;
+    uint2* d_edges = nullptr;
+    int2* d_pc = nullptr;
+    std::vector<int64_t> pc_host;  // 2n potential coordinates
+    double pot_scale = 0.0;
+    int pot_shift = 0;
+    ppsp_graph_info info{};
+    std::vector<uint64_t> deg;     // host copy of degrees (features, schedules)
+    // slot pool
+    std::multimap<ppsp::SlotKey, std::unique_ptr<ppsp::Slot>> pool;
+    bool pool_dirty = false;
+    std::mutex mu;
+    // scratch for small transfers (potential eval)
+    ppsp::u32* d_scratch_u32 = nullptr;
+    int64_t* d_scratch_i64 = nullptr;
+    uint64_t scratch_cap = 0;
+
+    ppsp::GraphDev dev() const {
+        ppsp::GraphDev g;
+        g.off = d_off;
+        g.edges = d_edges;
+        g.pc = d_pc;
+        g.n = (ppsp::u32)n;
+        g.pot_shift = (ppsp::u32)pot_shift;
+        return g;
+    }
+};
+
+namespace ppsp {
+
+// Borrow a slot with at least the requested capacities (allocating if needed).
+ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, Slot** out);
+void slot_release(ppsp_graph* g, Slot* s);
+// Restore the clean invariant of every pooled slot (after a failed run).
+ppsp_status pool_scrub(ppsp_graph* g, cudaStream_t stream);
+
+// Exact floor(sqrt(x)) on the host.
+u64 isqrt_host(u64 x);
+i64 pot_h_host(const ppsp_graph* g, u32 x, u32 v);
+
+}  // namespace ppsp

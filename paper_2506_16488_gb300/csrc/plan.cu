@@ -1,0 +1,583 @@
+// Batch planning: query graph (Sec. 5.1), groups, team schedule, launches.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <unordered_map>
+
+#include "graph_impl.h"
+
+using namespace ppsp;
+
+struct ppsp_plan {
+    ppsp_graph* g = nullptr;
+    ppsp_options opt{};
+    cudaStream_t stream = nullptr;
+    u64 k = 0;
+    int dist_bits = 32;
+    int block = 512;
+    u32 grid = 0;
+    std::vector<GroupDev> groups;
+    std::vector<SearchDev> searches;
+    std::vector<PartnerDev> partners;
+    std::vector<QEdgeDev> qedges;
+    std::vector<u32> map;              // input query -> global query edge, NONE for s == t
+    std::vector<std::pair<u32, u32>> qedge_ends;  // global query edge -> (s, t) vertices
+    std::vector<u32> team_first, team_size, team_queue, cta_team;
+    std::vector<u32> queue_items[MAX_QUEUES];
+    std::vector<Slot*> slots;
+    void* d_arena = nullptr;
+    size_t arena_bytes = 0;
+    char* d_runstate = nullptr;
+    size_t runstate_bytes = 0;
+    u32* d_map = nullptr;
+    EngineArgs args{};
+    bool launched = false;
+};
+
+namespace {
+
+struct UF {
+    std::vector<u32> p;
+    explicit UF(u32 n) : p(n) { std::iota(p.begin(), p.end(), 0u); }
+    u32 find(u32 x) {
+        while (p[x] != x) x = p[x] = p[p[x]];
+        return x;
+    }
+    void join(u32 a, u32 b) {
+        a = find(a);
+        b = find(b);
+        if (a != b) p[std::max(a, b)] = std::min(a, b);
+    }
+};
+
+u32 ceil_log2(u32 x) {
+    u32 s = 0;
+    while ((1u << s) < x) ++s;
+    return s;
+}
+
+ppsp_status check_options(const ppsp_graph* g, const ppsp_options& o) {
+    if (o.mode < PPSP_BIDS || o.mode > PPSP_ASTAR) return PPSP_ERR_INVALID_ARG;
+    if (o.dist_bits != 32 && o.dist_bits != 64) return PPSP_ERR_INVALID_ARG;
+    if (o.block_threads != 0 && o.block_threads != 256 && o.block_threads != 512 && o.block_threads != 1024)
+        return PPSP_ERR_INVALID_ARG;
+    if (o.frontier < PPSP_FRONTIER_AUTO || o.frontier > PPSP_FRONTIER_DENSE) return PPSP_ERR_INVALID_ARG;
+    if (o.layout < PPSP_LAYOUT_AUTO || o.layout > PPSP_LAYOUT_STACKED) return PPSP_ERR_INVALID_ARG;
+    if (o.batch_strategy < PPSP_BATCH_MULTI || o.batch_strategy > PPSP_BATCH_PLAIN) return PPSP_ERR_INVALID_ARG;
+    if (o.team_ctas < 0 || o.big_team_ctas < 0 || o.max_ctas < 0) return PPSP_ERR_INVALID_ARG;
+    const bool astar = o.mode == PPSP_BIDASTAR || o.mode == PPSP_ASTAR;
+    if (astar && !g->info.has_coords) return PPSP_ERR_NO_COORDS;
+    const bool bidir = o.mode == PPSP_BIDS || o.mode == PPSP_BIDASTAR;
+    if (bidir && !g->info.undirected) return PPSP_ERR_UNSUPPORTED;
+    return PPSP_OK;
+}
+
+}  // namespace
+
+// Build everything from host pairs.  Separated so ppsp_query can reuse it.
+static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64_t k, const ppsp_options* opt_in,
+                                    bool single_query, ppsp_plan** out) {
+    ppsp_options o;
+    if (opt_in)
+        o = *opt_in;
+    else
+        ppsp_options_init(&o);
+    ppsp_status st = check_options(g, o);
+    if (st != PPSP_OK) return st;
+    if (k && !pairs) return PPSP_ERR_INVALID_ARG;
+    const u64 n = g->n;
+    for (u64 q = 0; q < 2 * k; ++q)
+        if (pairs[q] >= n) return PPSP_ERR_INVALID_ARG;
+
+    auto P = std::make_unique<ppsp_plan>();
+    P->g = g;
+    P->opt = o;
+    P->k = k;
+    P->stream = (cudaStream_t)o.stream;
+    P->dist_bits = o.dist_bits;
+    const bool bidir = o.mode == PPSP_BIDS || o.mode == PPSP_BIDASTAR;
+    const u64 delta = o.delta ? o.delta : std::max<u64>(1, (u64)std::llround(g->info.w_mean));
+    const int strategy = single_query ? PPSP_BATCH_PLAIN : o.batch_strategy;
+
+    // ---- unique query edges ----
+    P->map.assign(k, NONE);
+    std::unordered_map<u64, u32> qe_id;
+    std::vector<std::pair<u32, u32>> uq;  // unique queries (s, t)
+    for (u64 q = 0; q < k; ++q) {
+        u32 s = pairs[2 * q], t = pairs[2 * q + 1];
+        if (s == t) continue;  // d(s, s) = 0, no search
+        u64 key = bidir ? (((u64)std::min(s, t) << 32) | std::max(s, t)) : (((u64)s << 32) | t);
+        auto it = qe_id.find(key);
+        if (it == qe_id.end()) {
+            it = qe_id.emplace(key, (u32)uq.size()).first;
+            uq.emplace_back(s, t);
+        }
+        P->map[q] = it->second;  // provisional: unique-query index, renumbered below
+    }
+    const u32 U = (u32)uq.size();
+
+    // ---- groups ----
+    // Each group: list of vertices (searches) and list of unique-query indices.
+    std::vector<std::vector<u32>> gverts, gqueries;
+    if (!bidir || strategy != PPSP_BATCH_MULTI) {
+        for (u32 u = 0; u < U; ++u) {
+            if (bidir)
+                gverts.push_back({uq[u].first, uq[u].second});
+            else
+                gverts.push_back({uq[u].first});
+            gqueries.push_back({u});
+        }
+    } else {
+        // Multi-BiDS: V_q = distinct endpoints, components of G_q (Sec. 5.2)
+        std::unordered_map<u32, u32> vid;
+        std::vector<u32> verts;
+        auto get = [&](u32 v) {
+            auto it = vid.find(v);
+            if (it != vid.end()) return it->second;
+            vid.emplace(v, (u32)verts.size());
+            verts.push_back(v);
+            return (u32)verts.size() - 1;
+        };
+        std::vector<std::pair<u32, u32>> le(U);
+        for (u32 u = 0; u < U; ++u) le[u] = {get(uq[u].first), get(uq[u].second)};
+        UF uf((u32)verts.size());
+        for (auto& e : le) uf.join(e.first, e.second);
+        std::unordered_map<u32, std::vector<u32>> comp_edges;
+        std::vector<u32> comp_order;
+        for (u32 u = 0; u < U; ++u) {
+            u32 r = uf.find(le[u].first);
+            auto it = comp_edges.find(r);
+            if (it == comp_edges.end()) {
+                comp_order.push_back(r);
+                it = comp_edges.emplace(r, std::vector<u32>()).first;
+            }
+            it->second.push_back(u);
+        }
+        for (u32 r : comp_order) {
+            // split components with more than KMAX vertices into sub-groups
+            std::vector<u32> cur_v, cur_q;
+            std::unordered_map<u32, u32> in_cur;
+            for (u32 u : comp_edges[r]) {
+                u32 a = le[u].first, b = le[u].second;
+                u32 need = (in_cur.count(a) ? 0 : 1) + (in_cur.count(b) ? 0 : 1);
+                if (cur_v.size() + need > (size_t)KMAX) {
+                    gverts.push_back(cur_v);
+                    gqueries.push_back(cur_q);
+                    cur_v.clear();
+                    cur_q.clear();
+                    in_cur.clear();
+                }
+                for (u32 x : {a, b})
+                    if (!in_cur.count(x)) {
+                        in_cur.emplace(x, (u32)cur_v.size());
+                        cur_v.push_back(verts[x]);
+                    }
+                cur_q.push_back(u);
+            }
+            gverts.push_back(cur_v);
+            gqueries.push_back(cur_q);
+        }
+    }
+
+    // ---- descriptors ----
+    const u32 NG = (u32)gverts.size();
+    std::vector<u32> uq_to_qe(U, NONE);
+    std::vector<double> gwork(NG, 1.0);
+    for (u32 gi = 0; gi < NG; ++gi) {
+        GroupDev G{};
+        const auto& V = gverts[gi];
+        const auto& Q = gqueries[gi];
+        G.sbeg = (u32)P->searches.size();
+        G.scnt = (u32)V.size();
+        G.qbeg = (u32)P->qedges.size();
+        G.qcnt = (u32)Q.size();
+        G.delta = delta;
+        if (bidir) {
+            G.mode = GM_BIDIR;
+            G.target = NONE;
+        } else {
+            G.mode = (o.mode == PPSP_ASTAR) ? GM_ASTAR : GM_ET;
+            G.target = uq[Q[0]].second;
+        }
+        if (G.scnt <= 2) {
+            G.layout = PPSP_LAYOUT_INTERLEAVED;
+            G.kshift = (G.scnt == 2) ? 1 : 0;
+        } else {
+            G.layout = (o.layout == PPSP_LAYOUT_STACKED) ? PPSP_LAYOUT_STACKED : PPSP_LAYOUT_INTERLEAVED;
+            G.kshift = ceil_log2(G.scnt);
+        }
+        const u64 range = G.layout == PPSP_LAYOUT_INTERLEAVED ? (n << G.kshift) : (u64)G.scnt * n;
+        if (range >= 0xFFFFFFFFull) return PPSP_ERR_UNSUPPORTED;
+        std::unordered_map<u32, u32> local;
+        for (u32 i = 0; i < G.scnt; ++i) local.emplace(V[i], i);
+        std::vector<std::vector<PartnerDev>> plist(G.scnt);
+        std::vector<i64> hmax(G.scnt, 0);
+        double work = 0.0;
+        for (u32 qi = 0; qi < G.qcnt; ++qi) {
+            u32 u = Q[qi];
+            u32 qe = G.qbeg + qi;
+            uq_to_qe[u] = qe;
+            QEdgeDev e;
+            e.a = local[uq[u].first];
+            e.b = bidir ? local[uq[u].second] : e.a;
+            P->qedges.push_back(e);
+            P->qedge_ends.emplace_back(uq[u].first, uq[u].second);
+            if (bidir) {
+                plist[e.a].push_back(PartnerDev{e.b, qe});
+                plist[e.b].push_back(PartnerDev{e.a, qe});
+            }
+            i64 h = g->info.has_coords ? pot_h_host(g, uq[u].first, uq[u].second) : 1;
+            hmax[e.a] = std::max(hmax[e.a], h);
+            hmax[e.b] = std::max(hmax[e.b], h);
+        }
+        for (u32 i = 0; i < G.scnt; ++i) {
+            SearchDev s{};
+            s.src = V[i];
+            s.pbeg = (u32)P->partners.size();
+            s.pcnt = (u32)plist[i].size();
+            for (auto& pd : plist[i]) P->partners.push_back(pd);
+            s.pot = 0;
+            s.pot_b = V[i];
+            s.key_off = 0;
+            if (o.mode == PPSP_BIDASTAR && s.pcnt == 1) {
+                // pair rule of Sec. 4.5: rho_i = h_partner - h_self
+                s.pot = 1;
+                s.pot_b = V[plist[i][0].j];
+                s.key_off = -pot_h_host(g, s.pot_b, s.src);
+            } else if (o.mode == PPSP_ASTAR) {
+                s.pot_b = G.target;
+                s.key_off = -pot_h_host(g, G.target, s.src);
+            }
+            P->searches.push_back(s);
+            work += (double)(hmax[i] + 1) * (double)(hmax[i] + 1) / 4.0;
+        }
+        gwork[gi] = work;
+        P->groups.push_back(G);
+    }
+    for (u64 q = 0; q < k; ++q)
+        if (P->map[q] != NONE) P->map[q] = uq_to_qe[P->map[q]];
+
+    // ---- launch shape ----
+    int block = o.block_threads ? o.block_threads : 512;
+    int bpsm = 0, sms = 0;
+    st = engine_occupancy(o.dist_bits, block, &bpsm, &sms);
+    if (st != PPSP_OK) return st;
+    if (bpsm < 1) return PPSP_ERR_UNSUPPORTED;
+    u32 grid = (u32)(bpsm * sms);
+    if (o.max_ctas > 0) grid = std::min<u32>(grid, (u32)o.max_ctas);
+    P->block = block;
+
+    // ---- teams and queues ----
+    std::vector<u32> big, small;
+    for (u32 gi = 0; gi < NG; ++gi) (P->groups[gi].scnt > 2 ? big : small).push_back(gi);
+    auto by_work = [&](u32 a, u32 b) { return gwork[a] > gwork[b]; };
+    std::stable_sort(big.begin(), big.end(), by_work);
+    std::stable_sort(small.begin(), small.end(), by_work);
+    struct TeamSpec {
+        u32 size, queue;
+    };
+    std::vector<TeamSpec> teams;
+    if (strategy == PPSP_BATCH_PLAIN) {
+        // one query (group) at a time on the whole GPU
+        u32 ts = o.team_ctas ? std::min<u32>(grid, (u32)o.team_ctas) : grid;
+        grid = ts;
+        teams.push_back({ts, 1});
+        P->queue_items[1] = big;
+        P->queue_items[1].insert(P->queue_items[1].end(), small.begin(), small.end());
+    } else {
+        double wb = 0, ws = 0;
+        for (u32 gi : big) wb += gwork[gi];
+        for (u32 gi : small) ws += gwork[gi];
+        u32 g_big = 0;
+        if (!big.empty() && small.empty())
+            g_big = grid;
+        else if (!big.empty())
+            g_big = std::min<u32>(grid - 1, std::max<u32>(1, (u32)std::llround(grid * wb / (wb + ws))));
+        u32 tb = 0, nbt = 0;
+        if (g_big) {
+            nbt = std::min<u32>((u32)big.size(), g_big);
+            tb = o.big_team_ctas ? std::min<u32>((u32)o.big_team_ctas, g_big) : g_big / nbt;
+            nbt = std::max<u32>(1, g_big / tb);
+            for (u32 t = 0; t < nbt; ++t) teams.push_back({tb, 0});
+        }
+        u32 g_small = grid - nbt * tb;
+        if (!small.empty() && g_small > 0) {
+            u32 ts = o.team_ctas ? std::min<u32>((u32)o.team_ctas, g_small) : 1;
+            u32 nst = std::max<u32>(1, g_small / ts);
+            for (u32 t = 0; t < nst; ++t) teams.push_back({ts, 1});
+            g_small = nst * ts;
+        } else {
+            g_small = 0;
+        }
+        grid = nbt * tb + g_small;
+        P->queue_items[0] = big;
+        P->queue_items[1] = small;
+    }
+    if (teams.empty() || grid == 0) {
+        teams.assign(1, {1, 1});
+        grid = 1;
+    }
+    P->grid = grid;
+    u32 first = 0;
+    for (u32 t = 0; t < teams.size(); ++t) {
+        P->team_first.push_back(first);
+        P->team_size.push_back(teams[t].size);
+        P->team_queue.push_back(teams[t].queue);
+        for (u32 c = 0; c < teams[t].size; ++c) P->cta_team.push_back(t);
+        first += teams[t].size;
+    }
+
+    // ---- slots ----
+    u64 range_q[MAX_QUEUES] = {0, 0};
+    for (u32 qd = 0; qd < MAX_QUEUES; ++qd)
+        for (u32 gi : P->queue_items[qd]) {
+            const GroupDev& G = P->groups[gi];
+            u64 range = G.layout == PPSP_LAYOUT_INTERLEAVED ? (n << G.kshift) : (u64)G.scnt * n;
+            range_q[qd] = std::max(range_q[qd], range);
+        }
+    for (u32 t = 0; t < teams.size(); ++t) {
+        u64 fc = std::max<u64>(range_q[teams[t].queue], 64);
+        fc = (fc + 63) & ~63ull;
+        u32 qcap = (o.frontier == PPSP_FRONTIER_SPARSE) ? (u32)fc : (u32)std::min<u64>(fc, fc / 8 + 4096);
+        u32 tcap = (u32)std::min<u64>(fc, fc / 4 + 4096);
+        if (teams[t].size == grid) tcap = (u32)fc;  // whole-GPU team: never overflow
+        Slot* s = nullptr;
+        st = slot_acquire(g, o.dist_bits, fc, qcap, tcap, &s);
+        if (st != PPSP_OK) {
+            for (Slot* x : P->slots) slot_release(g, x);
+            return st;
+        }
+        P->slots.push_back(s);
+    }
+
+    // ---- device arena ----
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const u32 NT = (u32)teams.size();
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o2 = off;
+        off += al(std::max<size_t>(bytes, 1));
+        return o2;
+    };
+    size_t o_groups = take(P->groups.size() * sizeof(GroupDev));
+    size_t o_search = take(P->searches.size() * sizeof(SearchDev));
+    size_t o_part = take(P->partners.size() * sizeof(PartnerDev));
+    size_t o_qe = take(P->qedges.size() * sizeof(QEdgeDev));
+    size_t o_ctat = take(P->cta_team.size() * 4);
+    size_t o_tf = take(NT * 4), o_tsz = take(NT * 4), o_tq = take(NT * 4);
+    size_t o_slots = take(NT * sizeof(SlotDev));
+    size_t o_q0 = take(P->queue_items[0].size() * 4), o_q1 = take(P->queue_items[1].size() * 4);
+    size_t o_map = take(k * 4);
+    size_t static_bytes = off;
+    size_t o_mu = take(P->qedges.size() * 8);
+    size_t o_mumax = take(P->searches.size() * 8);
+    size_t o_run = off;
+    size_t o_qh = take(MAX_QUEUES * 4);
+    size_t o_ts = take(NT * sizeof(TeamState));
+    size_t o_err = take(4);
+    size_t o_cnt = take(sizeof(EngineCounters));
+    P->runstate_bytes = off - o_run;
+    P->arena_bytes = off;
+    cudaError_t ce = cudaMalloc(&P->d_arena, P->arena_bytes);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        for (Slot* x : P->slots) slot_release(g, x);
+        return ce == cudaErrorMemoryAllocation ? PPSP_ERR_OOM : PPSP_ERR_CUDA;
+    }
+    char* base = (char*)P->d_arena;
+    std::vector<char> h(static_bytes, 0);
+    auto put = [&](size_t o2, const void* src, size_t bytes) {
+        if (bytes) memcpy(h.data() + o2, src, bytes);
+    };
+    put(o_groups, P->groups.data(), P->groups.size() * sizeof(GroupDev));
+    put(o_search, P->searches.data(), P->searches.size() * sizeof(SearchDev));
+    put(o_part, P->partners.data(), P->partners.size() * sizeof(PartnerDev));
+    put(o_qe, P->qedges.data(), P->qedges.size() * sizeof(QEdgeDev));
+    put(o_ctat, P->cta_team.data(), P->cta_team.size() * 4);
+    put(o_tf, P->team_first.data(), NT * 4);
+    put(o_tsz, P->team_size.data(), NT * 4);
+    put(o_tq, P->team_queue.data(), NT * 4);
+    std::vector<SlotDev> sd(NT);
+    for (u32 t = 0; t < NT; ++t) sd[t] = P->slots[t]->dev;
+    put(o_slots, sd.data(), NT * sizeof(SlotDev));
+    put(o_q0, P->queue_items[0].data(), P->queue_items[0].size() * 4);
+    put(o_q1, P->queue_items[1].data(), P->queue_items[1].size() * 4);
+    put(o_map, P->map.data(), k * 4);
+    ce = cudaMemcpy(base, h.data(), static_bytes, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return PPSP_ERR_CUDA;
+    }
+
+    EngineArgs& a = P->args;
+    a.g = g->dev();
+    a.groups = (const GroupDev*)(base + o_groups);
+    a.searches = (const SearchDev*)(base + o_search);
+    a.partners = (const PartnerDev*)(base + o_part);
+    a.qedges = (const QEdgeDev*)(base + o_qe);
+    a.mu = (u64*)(base + o_mu);
+    a.mumax = (u64*)(base + o_mumax);
+    a.cta_team = (const u32*)(base + o_ctat);
+    a.team_first = (const u32*)(base + o_tf);
+    a.team_size = (const u32*)(base + o_tsz);
+    a.team_queue = (const u32*)(base + o_tq);
+    a.tstate = (TeamState*)(base + o_ts);
+    a.slots = (SlotDev*)(base + o_slots);
+    a.queue_items[0] = (const u32*)(base + o_q0);
+    a.queue_items[1] = (const u32*)(base + o_q1);
+    a.queue_len[0] = (u32)P->queue_items[0].size();
+    a.queue_len[1] = (u32)P->queue_items[1].size();
+    a.queue_head = (u32*)(base + o_qh);
+    a.dense_den = o.dense_den ? o.dense_den : 16u;
+    a.frontier = (u32)o.frontier;
+    a.debug = o.debug_flags;
+    a.spin_limit = o.spin_limit ? o.spin_limit : (1ull << 26);
+    a.err = (u32*)(base + o_err);
+    a.counters = (EngineCounters*)(base + o_cnt);
+    P->d_runstate = base + o_run;
+    P->d_map = (u32*)(base + o_map);
+    *out = P.release();
+    return PPSP_OK;
+}
+
+static void plan_free(ppsp_plan* P) {
+    if (!P) return;
+    if (P->stream)
+        cudaStreamSynchronize(P->stream);
+    else
+        cudaDeviceSynchronize();
+    for (Slot* s : P->slots) slot_release(P->g, s);
+    cudaFree(P->d_arena);
+    cudaGetLastError();
+    delete P;
+}
+
+static ppsp_status plan_launch(ppsp_plan* P, u64* d_out) {
+    ppsp_status st = pool_scrub(P->g, P->stream);
+    if (st != PPSP_OK) return st;
+    PPSP_CUDA_TRY(cudaMemsetAsync(P->d_runstate, 0, P->runstate_bytes, P->stream));
+    if (!P->groups.empty()) {
+        st = launch_engine(P->args, P->dist_bits, P->block, P->grid, P->stream);
+        if (st != PPSP_OK) return st;
+    }
+    if (d_out) {
+        st = launch_scatter(P->d_map, P->args.mu, P->k, d_out, P->stream);
+        if (st != PPSP_OK) return st;
+    }
+    P->launched = true;
+    return PPSP_OK;
+}
+
+static ppsp_status plan_wait(ppsp_plan* P, ppsp_counters* counters) {
+    if (P->stream) {
+        PPSP_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    } else {
+        PPSP_CUDA_TRY(cudaDeviceSynchronize());
+    }
+    u32 err = 0;
+    EngineCounters ec{};
+    PPSP_CUDA_TRY(cudaMemcpy(&err, P->args.err, 4, cudaMemcpyDeviceToHost));
+    PPSP_CUDA_TRY(cudaMemcpy(&ec, P->args.counters, sizeof(ec), cudaMemcpyDeviceToHost));
+    if (counters) {
+        memset(counters, 0, sizeof(*counters));
+        counters->extracted = ec.extracted;
+        counters->edges = ec.edges;
+        counters->relaxed = ec.relaxed;
+        counters->pushed = ec.pushed;
+        counters->rounds = ec.rounds;
+        counters->groups = ec.groups;
+        counters->searches = ec.searches;
+        counters->touched = ec.touched;
+        counters->dense_rounds = ec.dense_rounds;
+    }
+    if (err) {
+        P->g->pool_dirty = true;
+        if (err & ERRB_TIMEOUT) return PPSP_ERR_TIMEOUT;
+        if (err & ERRB_OVERFLOW) return PPSP_ERR_OVERFLOW;
+        return PPSP_ERR_CUDA;
+    }
+    return PPSP_OK;
+}
+
+extern "C" {
+
+ppsp_status ppsp_plan_create(ppsp_graph* g, const uint32_t* pairs, uint64_t k, const ppsp_options* opt,
+                             ppsp_plan** out) {
+    if (!g || !out) return PPSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::lock_guard<std::mutex> lk(g->mu);
+    return plan_create_impl(g, pairs, k, opt, false, out);
+}
+
+ppsp_status ppsp_plan_run(ppsp_plan* p, uint64_t* d_dists_out) {
+    if (!p) return PPSP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(p->g->mu);
+    return plan_launch(p, d_dists_out);
+}
+
+ppsp_status ppsp_plan_sync(ppsp_plan* p, ppsp_counters* counters) {
+    if (!p) return PPSP_ERR_INVALID_ARG;
+    if (!p->launched) return PPSP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(p->g->mu);
+    return plan_wait(p, counters);
+}
+
+void ppsp_plan_destroy(ppsp_plan* p) {
+    if (!p) return;
+    ppsp_graph* g = p->g;
+    std::lock_guard<std::mutex> lk(g->mu);
+    plan_free(p);
+}
+
+static ppsp_status run_host(ppsp_graph* g, const uint32_t* pairs, uint64_t k, const ppsp_options* opt,
+                            bool single, uint64_t* dists_out, ppsp_counters* counters) {
+    ppsp_plan* P = nullptr;
+    ppsp_status st = plan_create_impl(g, pairs, k, opt, single, &P);
+    if (st != PPSP_OK) return st;
+    u64* d_out = nullptr;
+    cudaError_t ce = cudaMalloc(&d_out, std::max<u64>(1, k) * 8);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        plan_free(P);
+        return ce == cudaErrorMemoryAllocation ? PPSP_ERR_OOM : PPSP_ERR_CUDA;
+    }
+    st = plan_launch(P, d_out);
+    if (st == PPSP_OK) st = plan_wait(P, counters);
+    if (st == PPSP_OK && k) {
+        ce = cudaMemcpy(dists_out, d_out, k * 8, cudaMemcpyDeviceToHost);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            st = PPSP_ERR_CUDA;
+        }
+    }
+    cudaFree(d_out);
+    plan_free(P);
+    return st;
+}
+
+ppsp_status ppsp_query(ppsp_graph* g, uint32_t s, uint32_t t, const ppsp_options* opt, uint64_t* dist_out,
+                       uint32_t* path_buf, uint64_t path_cap, uint64_t* path_len) {
+    if (!g || !dist_out) return PPSP_ERR_INVALID_ARG;
+    if (opt && opt->want_paths) return PPSP_ERR_UNSUPPORTED;
+    (void)path_buf;
+    (void)path_cap;
+    if (path_len) *path_len = 0;
+    uint32_t pr[2] = {s, t};
+    std::lock_guard<std::mutex> lk(g->mu);
+    return run_host(g, pr, 1, opt, true, dist_out, nullptr);
+}
+
+ppsp_status ppsp_batch(ppsp_graph* g, const uint32_t* pairs, uint64_t k, const ppsp_options* opt,
+                       uint64_t* dists_out, uint32_t* paths_buf, const uint64_t* path_offsets, uint64_t* path_lens,
+                       ppsp_counters* counters) {
+    if (!g || (k && (!pairs || !dists_out))) return PPSP_ERR_INVALID_ARG;
+    if (opt && opt->want_paths) return PPSP_ERR_UNSUPPORTED;
+    (void)paths_buf;
+    (void)path_offsets;
+    (void)path_lens;
+    std::lock_guard<std::mutex> lk(g->mu);
+    return run_host(g, pairs, k, opt, false, dists_out, counters);
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// Internal declarations of the GB300 PPSP library (not part of the C ABI).
+//
+// Execution model.  A batch is a set of *groups*; a group is a set of k
+// single-source *searches* that share answers through *query edges* (a query
+// graph component, paper Sec. 5.1; a BiDS query is a group of two searches and
+// one query edge, Table 2).  One persistent cooperative kernel runs all groups.
+// Its CTAs are partitioned into *teams*; a team takes groups from its queue and
+// runs each to completion with the stepping loop of Alg. 2, synchronising its
+// CTAs once per step.  Every team owns a *slot*: the tentative-distance arrays,
+// the two frontier bitmaps, the two frontier queues and the touched list of the
+// group it is running.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ppsp.h"
+
+namespace ppsp {
+
+typedef uint32_t u32;
+typedef uint64_t u64;
+typedef int64_t i64;
+
+constexpr u64 INF64 = ~0ull;
+constexpr u32 INF32 = ~0u;
+constexpr u32 NONE = ~0u;
+constexpr int KMAX = 64;          // searches per group (query-graph vertices)
+constexpr int MAX_QUEUES = 2;     // group queues: 0 = multi-search groups, 1 = pairs/singles
+
+// Group modes (plug-ins of Table 2).
+enum : u32 {
+    GM_BIDIR = 0,    // BiDS / BiD-A* / Multi-BiDS: searches joined by query edges
+    GM_ET = 1,       // one-directional, early termination at target
+    GM_ASTAR = 2,    // one-directional A*
+    GM_SSSP = 3      // no target, no pruning (full single-source distances)
+};
+
+// Device error word bits.
+enum : u32 { ERRB_TIMEOUT = 1u, ERRB_OVERFLOW = 2u, ERRB_INTERNAL = 4u };
+
+struct GraphDev {
+    const u32* off;       // [n+1]
+    const uint2* edges;   // [m] (target, weight)
+    const int2* pc;       // [n] integer potential coordinates, or null
+    u32 n;
+    u32 pot_shift;        // F: h = isqrt(d2 >> 2F)
+};
+
+struct SearchDev {
+    u32 src;              // q_i
+    u32 pbeg, pcnt;       // partners[pbeg .. pbeg+pcnt)
+    u32 pot;              // 1: bidirectional A* potential rho_i(v) = h_{pot_b}(v) - h_{src}(v)
+    u32 pot_b;            // partner vertex of the potential
+    i64 key_off;          // added to keys so the source's key is 0
+};
+
+struct PartnerDev {
+    u32 j;                // local index of the partner search in the group
+    u32 qe;               // global query-edge index
+};
+
+struct QEdgeDev {
+    u32 a, b;             // local search indices (a == b for one-directional groups)
+};
+
+struct GroupDev {
+    u32 sbeg, scnt;       // searches[sbeg .. sbeg+scnt)
+    u32 qbeg, qcnt;       // query edges
+    u32 mode;             // GM_*
+    u32 target;           // ET / A*: target vertex
+    u32 layout;           // PPSP_LAYOUT_INTERLEAVED or PPSP_LAYOUT_STACKED
+    u32 kshift;           // interleaved: flat = (v << kshift) | i
+    u64 delta;            // stepping increment
+};
+
+// Per-slot step state, triple buffered by step index (cur, next, reset).
+struct StepState {
+    u64 minkey;           // min key inserted into this step's frontier
+    u32 count;            // distinct entries in this step's frontier (queue tail when sparse)
+    u32 tile;             // dynamic tile counter while the step is processed
+    u32 overflow;         // queue overflowed: step must be processed from the bitmap
+    u32 cnt_dir[2];       // entries per direction (two-search groups)
+    u32 pad;
+};
+
+struct SlotState {
+    StepState s[3];
+    u32 touched_n;
+    u32 touched_overflow;
+    u32 pad[2];
+};
+
+struct SlotDev {
+    void* dist;           // tentative distances, flat_cap entries of DistT
+    u32* bm[2];           // frontier bitmaps, flat_cap bits each
+    u32* q[2];            // frontier queues, qcap entries each
+    u32* touched;         // flat indices that left infinity, tcap entries
+    SlotState* st;
+    u64 flat_cap;         // k_cap * n
+    u32 qcap, tcap;
+};
+
+struct TeamState {
+    u32 bar_count;
+    u32 bar_gen;
+    u32 group;
+    u32 pad[29];          // one 128-byte line per team
+};
+
+struct EngineCounters {
+    unsigned long long extracted, edges, relaxed, pushed, rounds, groups, searches, touched,
+        dense_rounds;
+};
+
+struct EngineArgs {
+    GraphDev g;
+    const GroupDev* groups;
+    const SearchDev* searches;
+    const PartnerDev* partners;
+    const QEdgeDev* qedges;
+    u64* mu;              // [num_qedges]
+    u64* mumax;           // [num_searches]
+    // teams
+    const u32* cta_team;  // [grid] team of each CTA
+    const u32* team_first;// [teams] first CTA
+    const u32* team_size; // [teams]
+    const u32* team_queue;// [teams] group queue
+    TeamState* tstate;    // [teams]
+    SlotDev* slots;       // [teams]
+    const u32* queue_items[MAX_QUEUES];
+    u32 queue_len[MAX_QUEUES];
+    u32* queue_head;      // [MAX_QUEUES] claim counters
+    // options
+    u32 dense_den;        // dense when count > flat_size / dense_den (0 = never)
+    u32 frontier;         // PPSP_FRONTIER_*
+    u32 debug;
+    u64 spin_limit;
+    u32* err;
+    EngineCounters* counters;
+};
+
+// ---- host helpers shared between translation units ----
+#define PPSP_CUDA_TRY(expr)                                          \
+    do {                                                              \
+        cudaError_t e__ = (expr);                                     \
+        if (e__ != cudaSuccess) {                                     \
+            ppsp::set_last_cuda_error(e__, #expr, __FILE__, __LINE__); \
+            return e__ == cudaErrorMemoryAllocation ? PPSP_ERR_OOM : PPSP_ERR_CUDA; \
+        }                                                             \
+    } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// Launch the persistent engine.  dist_bits selects the distance width.
+ppsp_status launch_engine(const EngineArgs& a, int dist_bits, int block_threads, u32 grid,
+                          cudaStream_t stream);
+
+// Max resident CTAs of the engine for a block size / distance width.
+ppsp_status engine_occupancy(int dist_bits, int block_threads, int* blocks_per_sm, int* sms);
+
+// Evaluate potentials h_anchor(v) on the device.
+ppsp_status launch_potential_eval(const GraphDev& g, u32 anchor, const u32* d_verts, u64 count,
+                                  i64* d_out, cudaStream_t stream);
+
+// Result scatter out[q] = (map[q] == NONE) ? 0 : mu[map[q]].
+ppsp_status launch_scatter(const u32* d_map, const u64* d_mu, u64 k, u64* d_out, cudaStream_t s);
+
+}  // namespace ppsp

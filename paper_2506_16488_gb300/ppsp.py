@@ -1,0 +1,297 @@
+"""Python binding of the C ABI in include/ppsp.h (argument marshalling only).
+
+Every search step runs in the CUDA library lib/libppsp.so.  There is no
+fallback: if the library is missing or cannot load, :func:`load` raises.
+Names follow the C ABI (ppsp_graph_create -> Graph, ppsp_query -> Graph.query,
+ppsp_batch -> Graph.batch, ppsp_plan_* -> Plan).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+INF = 0xFFFFFFFFFFFFFFFF
+
+# status codes
+OK, ERR_INVALID_ARG, ERR_BAD_GRAPH, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_COORDS, \
+    ERR_BUFFER_TOO_SMALL, ERR_OVERFLOW, ERR_UNSUPPORTED = range(10)
+STATUS_NAMES = ["OK", "INVALID_ARG", "BAD_GRAPH", "OOM", "CUDA", "TIMEOUT", "NO_COORDS",
+                "BUFFER_TOO_SMALL", "OVERFLOW", "UNSUPPORTED"]
+
+MODES = {"bids": 0, "bidastar": 1, "et": 2, "astar": 3}
+FRONTIER = {"auto": 0, "sparse": 1, "dense": 2}
+LAYOUT = {"auto": 0, "interleaved": 1, "stacked": 2}
+STRATEGY = {"multi": 0, "plain_star": 1, "plain": 2}
+UNDIRECTED = 1
+DEBUG_BARRIER_NEVER_RELEASES = 1
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int32),
+        ("dist_bits", ctypes.c_int32),
+        ("delta", ctypes.c_uint64),
+        ("frontier", ctypes.c_int32),
+        ("layout", ctypes.c_int32),
+        ("batch_strategy", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+        ("team_ctas", ctypes.c_int32),
+        ("big_team_ctas", ctypes.c_int32),
+        ("dense_den", ctypes.c_uint32),
+        ("want_paths", ctypes.c_int32),
+        ("max_ctas", ctypes.c_int32),
+        ("spin_limit", ctypes.c_uint64),
+        ("stream", ctypes.c_void_p),
+        ("debug_flags", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 7),
+    ]
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in
+                ("extracted", "edges", "relaxed", "pushed", "rounds", "groups", "searches",
+                 "touched", "dense_rounds")] + [("reserved", ctypes.c_uint64 * 7)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64), ("m", ctypes.c_uint64),
+        ("w_min", ctypes.c_uint64), ("w_max", ctypes.c_uint64),
+        ("w_mean", ctypes.c_double), ("w_std", ctypes.c_double),
+        ("deg_max", ctypes.c_uint64),
+        ("potential_scale", ctypes.c_double),
+        ("potential_shift", ctypes.c_int32),
+        ("has_coords", ctypes.c_int32),
+        ("undirected", ctypes.c_int32),
+        ("has_zero_weight", ctypes.c_int32),
+        ("device_bytes", ctypes.c_uint64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class PPSPError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{what}: PPSP_ERR_{name}" if what else f"PPSP_ERR_{name}")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load lib/libppsp.so (raises if absent unless build_if_missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise RuntimeError(f"{_build.LIB} is missing: run __graft_entry__.build() first")
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        p, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32
+        S = ctypes.c_int
+        sig = {
+            "ppsp_options_init": (None, [p]),
+            "ppsp_status_string": (ctypes.c_char_p, [S]),
+            "ppsp_last_error_detail": (ctypes.c_char_p, []),
+            "ppsp_graph_create": (S, [u64, u64, p, p, p, p, u32, p]),
+            "ppsp_graph_destroy": (None, [p]),
+            "ppsp_graph_get_info": (S, [p, p]),
+            "ppsp_query": (S, [p, u32, u32, p, p, p, u64, p]),
+            "ppsp_batch": (S, [p, p, u64, p, p, p, p, p, p]),
+            "ppsp_plan_create": (S, [p, p, u64, p, p]),
+            "ppsp_plan_run": (S, [p, p]),
+            "ppsp_plan_sync": (S, [p, p]),
+            "ppsp_plan_destroy": (None, [p]),
+            "ppsp_potential_coords": (S, [p, p]),
+            "ppsp_potential_eval": (S, [p, u32, p, u64, p]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        detail = ""
+        if status == ERR_CUDA:
+            d = load().ppsp_last_error_detail()
+            detail = f" ({d.decode()})" if d else ""
+        raise PPSPError(status, what + detail)
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, frontier="auto",
+                 layout="auto", strategy="multi", block_threads: int = 0, team_ctas: int = 0,
+                 big_team_ctas: int = 0, dense_den: int = 0, want_paths: bool = False, max_ctas: int = 0,
+                 spin_limit: int = 0, stream: int | None = None, debug_flags: int = 0) -> Options:
+    o = Options()
+    load().ppsp_options_init(ctypes.byref(o))
+    o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+    o.dist_bits = dist_bits
+    o.delta = delta
+    o.frontier = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
+    o.layout = LAYOUT[layout] if isinstance(layout, str) else int(layout)
+    o.batch_strategy = STRATEGY[strategy] if isinstance(strategy, str) else int(strategy)
+    o.block_threads = block_threads
+    o.team_ctas = team_ctas
+    o.big_team_ctas = big_team_ctas
+    o.dense_den = dense_den
+    o.want_paths = int(bool(want_paths))
+    o.max_ctas = max_ctas
+    o.spin_limit = spin_limit
+    o.stream = stream
+    o.debug_flags = debug_flags
+    return o
+
+
+class Graph:
+    """Device-resident CSR graph (ppsp_graph_create / ppsp_graph_destroy)."""
+
+    def __init__(self, offsets, targets, weights, coords=None, undirected: bool = True):
+        lib = load()
+        self._off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        tgt = np.ascontiguousarray(targets, dtype=np.uint32)
+        w = np.ascontiguousarray(weights, dtype=np.uint32)
+        xy = None if coords is None else np.ascontiguousarray(coords, dtype=np.float32).reshape(-1)
+        n = self._off.shape[0] - 1
+        h = ctypes.c_void_p()
+        st = lib.ppsp_graph_create(n, tgt.shape[0], _ptr(self._off), _ptr(tgt), _ptr(w), _ptr(xy),
+                                   UNDIRECTED if undirected else 0, ctypes.byref(h))
+        _check(st, "ppsp_graph_create")
+        self._h = h
+        self.n = n
+        self.m = int(tgt.shape[0])
+
+    @classmethod
+    def from_csr(cls, g, undirected: bool = True, with_coords: bool = True):
+        return cls(g.offsets, g.targets, g.weights, g.coords if with_coords else None, undirected)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ppsp_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def info(self) -> dict:
+        gi = GraphInfo()
+        _check(load().ppsp_graph_get_info(self._h, ctypes.byref(gi)), "ppsp_graph_get_info")
+        return gi.as_dict()
+
+    def query(self, s: int, t: int, **opts) -> int:
+        o = make_options(**opts)
+        d = ctypes.c_uint64(0)
+        plen = ctypes.c_uint64(0)
+        st = load().ppsp_query(self._h, s, t, ctypes.byref(o), ctypes.byref(d), None, 0, ctypes.byref(plen))
+        _check(st, "ppsp_query")
+        return int(d.value)
+
+    def query_status(self, s: int, t: int, **opts) -> tuple:
+        """(status, distance) without raising (for error-path tests)."""
+        o = make_options(**opts)
+        d = ctypes.c_uint64(0)
+        st = load().ppsp_query(self._h, s, t, ctypes.byref(o), ctypes.byref(d), None, 0, None)
+        return int(st), int(d.value)
+
+    def batch(self, pairs, return_counters: bool = False, **opts):
+        o = make_options(**opts)
+        pa = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+        k = pa.shape[0]
+        out = np.zeros(k, dtype=np.uint64)
+        c = Counters()
+        st = load().ppsp_batch(self._h, _ptr(pa), k, ctypes.byref(o), _ptr(out), None, None, None,
+                               ctypes.byref(c))
+        _check(st, "ppsp_batch")
+        return (out, c.as_dict()) if return_counters else out
+
+    def batch_status(self, pairs, **opts) -> tuple:
+        o = make_options(**opts)
+        pa = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+        out = np.zeros(pa.shape[0], dtype=np.uint64)
+        st = load().ppsp_batch(self._h, _ptr(pa), pa.shape[0], ctypes.byref(o), _ptr(out), None, None,
+                               None, None)
+        return int(st), out
+
+    def plan(self, pairs, **opts) -> "Plan":
+        return Plan(self, pairs, **opts)
+
+    def potential_coords(self) -> np.ndarray:
+        out = np.empty(2 * self.n, dtype=np.int64)
+        _check(load().ppsp_potential_coords(self._h, _ptr(out)), "ppsp_potential_coords")
+        return out.reshape(-1, 2)
+
+    def potential_eval(self, anchor: int, vertices) -> np.ndarray:
+        v = np.ascontiguousarray(vertices, dtype=np.uint32)
+        out = np.empty(v.shape[0], dtype=np.int64)
+        _check(load().ppsp_potential_eval(self._h, anchor, _ptr(v), v.shape[0], _ptr(out)),
+               "ppsp_potential_eval")
+        return out
+
+
+class Plan:
+    """A prepared batch (ppsp_plan_create); run() writes distances to a device buffer."""
+
+    def __init__(self, graph: Graph, pairs, **opts):
+        self.graph = graph
+        self._opts = make_options(**opts)
+        pa = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+        self.k = pa.shape[0]
+        h = ctypes.c_void_p()
+        _check(load().ppsp_plan_create(graph._h, _ptr(pa), self.k, ctypes.byref(self._opts), ctypes.byref(h)),
+               "ppsp_plan_create")
+        self._h = h
+
+    def run(self, d_out_ptr: int):
+        _check(load().ppsp_plan_run(self._h, ctypes.c_void_p(d_out_ptr)), "ppsp_plan_run")
+
+    def sync(self) -> dict:
+        c = Counters()
+        _check(load().ppsp_plan_sync(self._h, ctypes.byref(c)), "ppsp_plan_sync")
+        return c.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ppsp_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
