@@ -392,7 +392,6 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
     u32 excl = block_excl_scan<B>(deg, sm, &total);
     sm.pre[t] = (t < cnt) ? excl : total;
     __syncthreads();
-    c.c_e += 0;
     for (u32 e = t; e < total; e += B) {
         u32 lo = 0, hi = cnt;
         while (hi - lo > 1) {
@@ -448,8 +447,8 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
             slot.q[0][t] = f;
             slot.touched[t] = f;
         }
-        if (t < G.qcnt) {
-            QEdgeDev e = a.qedges[G.qbeg + t];
+        for (u32 q = t; q < G.qcnt; q += B) {
+            QEdgeDev e = a.qedges[G.qbeg + q];
             u64 m;
             if (G.mode == GM_BIDIR)
                 m = (sm.src[e.a] == sm.src[e.b]) ? 0 : INF64;
@@ -457,7 +456,7 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
                 m = INF64;
             else
                 m = (sm.src[0] == G.target) ? 0 : INF64;
-            a.mu[G.qbeg + t] = m;
+            a.mu[G.qbeg + q] = m;
         }
         if (t == 0) {
             S[0].count = G.scnt;
@@ -631,15 +630,17 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
                 st_dist(c.dist + __ldcg(slot.touched + k), DT<D>::INF);
         }
     }
+    // order of EngineCounters: extracted, edges, relaxed, pushed, rounds,
+    // groups, searches, touched, dense_rounds
     cnt_acc[0] += c.c_x;
     cnt_acc[1] += c.c_e;
     cnt_acc[2] += c.c_r;
     cnt_acc[3] += c.c_p;
-    cnt_acc[4] += c.c_t;
+    cnt_acc[7] += c.c_t;
     if (t == 0 && tc.rank == 0) {
-        cnt_acc[5] += rounds;
-        cnt_acc[6] += 1;
-        cnt_acc[7] += G.scnt;
+        cnt_acc[4] += rounds;
+        cnt_acc[5] += 1;
+        cnt_acc[6] += G.scnt;
         cnt_acc[8] += dense_rounds;
     }
     return team_sync(tc, a, &sm.flag);
