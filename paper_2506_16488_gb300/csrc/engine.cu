@@ -126,7 +126,11 @@ __device__ bool team_sync(const TeamCtx& tc, const EngineArgs& a, u32* s_flag) {
         } else {
             u64 it = 0;
             while (ld_volatile(&tc.ts->bar_gen) == gen) {
-                if (++it > a.spin_limit || ld_volatile(a.err) != 0) {
+                if (ld_volatile(a.err) != 0) {  // another CTA failed: leave
+                    ok = 0;
+                    break;
+                }
+                if (++it > a.spin_limit) {
                     atomicOr(a.err, ERRB_TIMEOUT);
                     ok = 0;
                     break;

@@ -240,8 +240,12 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
             s.pot = 0;
             s.pot_b = V[i];
             s.key_off = 0;
-            if (o.mode == PPSP_BIDASTAR && s.pcnt == 1) {
-                // pair rule of Sec. 4.5: rho_i = h_partner - h_self
+            if (o.mode == PPSP_BIDASTAR && G.scnt == 2) {
+                // Sec. 4.5 for an isolated pair: rho_i = h_partner - h_self, so the
+                // two searches use exactly opposite potentials (h_F = -h_B, which
+                // Theorem 4.2 relies on).  Searches of larger query-graph components
+                // run without a potential: a shared search cannot hold the opposite
+                // of every partner's potential at once.
                 s.pot = 1;
                 s.pot_b = V[plist[i][0].j];
                 s.key_off = -pot_h_host(g, s.pot_b, s.src);
@@ -493,8 +497,8 @@ static ppsp_status plan_wait(ppsp_plan* P, ppsp_counters* counters) {
     }
     if (err) {
         P->g->pool_dirty = true;
-        if (err & ERRB_TIMEOUT) return PPSP_ERR_TIMEOUT;
         if (err & ERRB_OVERFLOW) return PPSP_ERR_OVERFLOW;
+        if (err & ERRB_TIMEOUT) return PPSP_ERR_TIMEOUT;
         return PPSP_ERR_CUDA;
     }
     return PPSP_OK;

@@ -236,7 +236,9 @@ def test_plan_writes_device_output(cfg1):
         plan.run(out.data_ptr())
         cnt = plan.sync()
         assert np.array_equal(out.cpu().numpy().view(np.uint64), want)
-        assert cnt["searches"] == 2 * np.count_nonzero(pairs[:, 0] != pairs[:, 1])
+        # Multi-BiDS: one search per distinct endpoint of the query graph (Sec. 5.2)
+        uniq = {(min(a, b), max(a, b)) for a, b in pairs.tolist() if a != b}
+        assert cnt["searches"] == len({v for e in uniq for v in e})
     plan.close()
 
 
