@@ -229,8 +229,18 @@ def run_ours(args):
     G = ppsp.Graph.from_csr(g)
     stream = torch.cuda.Stream()
     opts = dict(mode=mode, strategy="multi", stream=stream.cuda_stream)
+    delta_rule = "default (mean edge weight)"
+    model = None
     if args.delta:
         opts["delta"] = args.delta
+        delta_rule = f"fixed {args.delta}"
+    elif not args.no_learned:
+        from paper_2506_16488_gb300 import learned_delta
+
+        model = learned_delta.load_model(mode)
+        if model is not None:
+            G.set_delta_model(mode, model)
+            delta_rule = f"learned MLP ({os.path.relpath(learned_delta.weights_path(mode), ROOT)})"
     plan = G.plan(pairs, **opts)
     out = torch.zeros(k, dtype=torch.int64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -277,19 +287,30 @@ def run_ours(args):
         e2e_ms.append(1000 * (time.perf_counter() - t0))
     assert np.array_equal(res, got)
 
-    # plain: one query at a time on the whole GPU
-    plain_plan = G.plan(pairs, mode=mode, strategy="plain", stream=stream.cuda_stream,
-                        **({"delta": args.delta} if args.delta else {}))
-    plain_out = torch.zeros(k, dtype=torch.int64, device="cuda")
-    plain_plan.run(plain_out.data_ptr())
-    plain_plan.sync()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    plain_plan.run(plain_out.data_ptr())
-    e1.record(stream)
-    plain_cnt = plain_plan.sync()
-    plain_ms = e0.elapsed_time(e1)
-    assert np.array_equal(plain_out.cpu().numpy().view(np.uint64), got)
+    # plain: one query at a time on the whole GPU (Plain-BiDS), with the
+    # default Delta and with the same Delta rule as the batched run
+    default_delta = max(1, int(round(G.info()["w_mean"])))
+
+    def run_plain(**popts):
+        pp = G.plan(pairs, mode=mode, strategy="plain", stream=stream.cuda_stream, **popts)
+        po = torch.zeros(k, dtype=torch.int64, device="cuda")
+        pp.run(po.data_ptr())
+        pp.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pp.run(po.data_ptr())
+        e1.record(stream)
+        pc = pp.sync()
+        ms = e0.elapsed_time(e1)
+        assert np.array_equal(po.cpu().numpy().view(np.uint64), got)
+        pp.close()
+        return {"value": k / (ms / 1000.0), "unit": "queries/s", "ms": ms,
+                "gteps": pc["edges"] / (ms / 1000.0) / 1e9, "rounds": pc["rounds"]}
+
+    plain = run_plain(delta=args.delta or default_delta)
+    plain["delta"] = f"default {default_delta}" if not args.delta else f"fixed {args.delta}"
+    plain_same = run_plain(**({"delta": args.delta} if args.delta else {}))
+    plain_same["delta"] = delta_rule
 
     if rank != 0:
         return
@@ -315,14 +336,15 @@ def run_ours(args):
         "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": workload, "queries_per_step": k, "strategy": "multi (query graph)",
-                   "delta": args.delta or "default (mean edge weight)",
+                   "delta": delta_rule,
                    "l2": "flushed between steps (256 MB write)",
                    "inputs": "plan (query graph, schedule) built before the timed region; graph, plan and "
                              "output resident in HBM", "parallelism": f"replicas x{world}"},
         "gteps": cnt["edges"] / (ms_per_step / 1000.0) / 1e9,
-        "plain": {"value": k / (plain_ms / 1000.0), "unit": "queries/s", "ms": plain_ms,
-                  "gteps": plain_cnt["edges"] / (plain_ms / 1000.0) / 1e9},
-        "speedup_vs_plain": qps / world / (k / (plain_ms / 1000.0)),
+        "plain": plain,
+        "plain_same_delta": plain_same,
+        "speedup_vs_plain": qps / world / plain["value"],
+        "speedup_vs_plain_same_delta": qps / world / plain_same["value"],
         "counters": cnt,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
@@ -336,7 +358,6 @@ def run_ours(args):
     }
     print(json.dumps(line), flush=True)
     plan.close()
-    plain_plan.close()
     G.close()
     if world > 1:
         dist.destroy_process_group()
@@ -350,6 +371,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--delta", type=int, default=0)
+    ap.add_argument("--no-learned", action="store_true", help="use the default Delta, not the learned model")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

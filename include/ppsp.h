@@ -236,6 +236,61 @@ ppsp_status ppsp_potential_coords(const ppsp_graph* g, int64_t* out);
 ppsp_status ppsp_potential_eval(ppsp_graph* g, uint32_t anchor, const uint32_t* vertices,
                                 uint64_t count, int64_t* out);
 
+/*
+ * Features of each group of a plan, as the stepping-increment model sees them:
+ * out[12 * g + f] = log2(1 + raw_f) for f = heuristic s-t distance (mean over
+ * the group's queries, 0 without coordinates), deg(s), deg(t) (for groups of
+ * more than two searches: mean and max degree), mean/std/min/max edge weight,
+ * n, m, |V_q|, |E_q| of the group and its mean query-graph degree.
+ *   out     host float[12 * cap] or NULL (then only *ngroups is written)
+ * Errors: INVALID_ARG, BUFFER_TOO_SMALL (cap < number of groups).
+ */
+ppsp_status ppsp_plan_features(const ppsp_plan* p, float* out, uint64_t cap, uint64_t* ngroups);
+
+/*
+ * Device time of every group in the plan's last run (ns between the group's
+ * Init and the end of its tidy step, on the team that ran it); waits for the
+ * plan's stream.  out_ns host uint64[cap] or NULL (then only *ngroups).
+ * Used to label the stepping-increment sweep.  Errors: INVALID_ARG (never
+ * run), BUFFER_TOO_SMALL, CUDA.
+ */
+ppsp_status ppsp_plan_group_times(ppsp_plan* p, uint64_t* out_ns, uint64_t cap, uint64_t* ngroups);
+
+/*
+ * Learned stepping increment.  The paper tunes Delta of Delta*-stepping by
+ * doubling it until the time stops improving (Sec. 7.1); Delta changes only
+ * the schedule, never an answer (Theorems 4.1/4.2).  This library predicts it
+ * per group with a 12 -> 64 -> 64 -> 1 MLP (ReLU; bf16 weights, fp32
+ * accumulation): y = log2(Delta / Delta_default), Delta_default = mean edge
+ * weight, Delta = round(Delta_default * 2^clamp(y, -8, 6)), at least 1.
+ * Parameter vector: PPSP_MLP_PARAMS floats, in order mean[12], std[12]
+ * (input standardisation, std > 0), W1[64][12], b1[64], W2[64][64], b2[64],
+ * W3[64], b3[1].  A model lives on the device until destroyed.
+ *   create:     copies params (host).  Errors: INVALID_ARG (std <= 0), OOM, CUDA.
+ *   get_params: host float[PPSP_MLP_PARAMS] receives the fp32 master copy.
+ *   predict:    host feats[12 * count] -> host out[count] (y per sample).
+ *   grad:       gradient of mean((y - labels)^2) w.r.t. every parameter
+ *               (zero for mean/std) into host grad_out[PPSP_MLP_PARAMS];
+ *               *loss_out (nullable) = that mean.
+ *   train:      `epochs` full-batch Adam steps (beta 0.9/0.999, eps 1e-8) at
+ *               learning rate lr; *loss_out (nullable) = loss before the last step.
+ *   graph_set_delta_model: plans of mode `mode` created afterwards with
+ *               delta = 0 use the model (borrowed: keep it alive while such
+ *               plans run; NULL detaches).
+ */
+#define PPSP_MLP_FEATURES 12
+#define PPSP_MLP_PARAMS 5081
+typedef struct ppsp_delta_model ppsp_delta_model;
+ppsp_status ppsp_delta_model_create(const float* params, ppsp_delta_model** out);
+void ppsp_delta_model_destroy(ppsp_delta_model* m);
+ppsp_status ppsp_delta_model_get_params(const ppsp_delta_model* m, float* out);
+ppsp_status ppsp_delta_model_predict(ppsp_delta_model* m, const float* feats, uint64_t count, float* out);
+ppsp_status ppsp_delta_model_grad(ppsp_delta_model* m, const float* feats, const float* labels, uint64_t count,
+                                  float* grad_out, float* loss_out);
+ppsp_status ppsp_delta_model_train(ppsp_delta_model* m, const float* feats, const float* labels, uint64_t count,
+                                   uint32_t epochs, float lr, float* loss_out);
+ppsp_status ppsp_graph_set_delta_model(ppsp_graph* g, int32_t mode, ppsp_delta_model* m);
+
 #ifdef __cplusplus
 }
 #endif

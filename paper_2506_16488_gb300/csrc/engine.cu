@@ -76,6 +76,11 @@ __device__ __forceinline__ u64 amin64(u64* p, u64 v) {
     return (u64)atomicMin(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
 __device__ __forceinline__ u32 ld_volatile(const u32* p) { return *reinterpret_cast<const volatile u32*>(p); }
+__device__ __forceinline__ u64 global_ns() {
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Exact floor(sqrt(x)) for x < 2^62: float64 estimate, then integer correction.
 __device__ __forceinline__ u64 isqrt_u64(u64 x) {
@@ -148,16 +153,23 @@ __device__ bool team_sync(const TeamCtx& tc, const EngineArgs& a, u32* s_flag) {
 // ----------------------------------------------------------------------------
 // shared memory
 // ----------------------------------------------------------------------------
+constexpr u32 QSTAGE = 1024;  // staged frontier appends per CTA and tile
+constexpr u32 TSTAGE = 512;   // staged touched-list appends per CTA and tile
+constexpr u32 PCAP = 1024;    // partner entries of a group cached in shared memory
+
 template <int B>
 struct Smem {
     // tile of frontier entries
     u32 flat[B];
-    u32 v[B];
     u32 beg[B];
     u32 pre[B];
     u64 d[B];
     unsigned char si[B];
     u32 wsum[B / 32];
+    // staging of appends
+    u32 qbuf[QSTAGE];
+    u32 tbuf[TSTAGE];
+    u32 qn, tn, qbase, tbase;
     // group cache
     u32 src[KMAX];
     u32 pbeg[KMAX];
@@ -167,8 +179,10 @@ struct Smem {
     int2 pb[KMAX];
     i64 key_off[KMAX];
     u64 bound[KMAX];
+    PartnerDev pcache[PCAP];
+    u32 pcached, pot_any;
     // step scalars
-    u64 minkey;
+    u64 minkey_in, minkey_acc;
     u32 count, overflow, dir0, dir1, tile, flag, total, nitems;
     u32 cnt_dir[2];
     u32 group;
@@ -216,6 +230,7 @@ struct GCtx {
     SlotDev slot;
     u64 theta;
     bool dense_nxt;
+    bool pair;        // two searches, interleaved: both distances of v share 2*W bytes
     u32 n;
     // per-thread counters
     u64 c_x, c_e, c_r, c_p, c_t;
@@ -234,20 +249,31 @@ __device__ __forceinline__ void decode_flat(const GroupDev& G, u32 n, u32 f, u32
     }
 }
 
-// key and prune value of <v, i> at tentative distance d
+// Both tentative distances of vertex v in a pair group, one 2W-byte load.
+__device__ __forceinline__ void ld_pair(const u32* d, u32 v, u64& x0, u64& x1) {
+    uint2 p = __ldcg(reinterpret_cast<const uint2*>(d) + v);
+    x0 = p.x;
+    x1 = p.y;
+}
+__device__ __forceinline__ void ld_pair(const u64* d, u32 v, u64& x0, u64& x1) {
+    ulonglong2 p = __ldcg(reinterpret_cast<const ulonglong2*>(d) + v);
+    x0 = p.x;
+    x1 = p.y;
+}
+
+// key and prune value of <v, i> at tentative distance d; pv2 = P(v) when a
+// potential is used (prefetched by the caller)
 template <int B>
 __device__ __forceinline__ void key_pv(const EngineArgs& a, const GroupDev& G, const Smem<B>& sm,
-                                       u32 i, u32 v, u64 d, i64& key, i64& pv) {
+                                       u32 i, int2 pv2, u64 d, i64& key, i64& pv) {
     if (G.mode == GM_BIDIR) {
         i64 rho = 0;
-        if (sm.pot[i]) {
-            int2 pv2 = a.g.pc[v];
+        if (sm.pot[i])
             rho = pot_h(sm.pb[i], pv2, a.g.pot_shift) - pot_h(sm.pa[i], pv2, a.g.pot_shift);
-        }
         pv = 2 * (i64)d + rho;
         key = pv + sm.key_off[i];
     } else if (G.mode == GM_ASTAR) {
-        i64 ht = pot_h(sm.pb[0], a.g.pc[v], a.g.pot_shift);
+        i64 ht = pot_h(sm.pb[0], pv2, a.g.pot_shift);
         pv = (i64)d + ht;
         key = pv + sm.key_off[0];
     } else {
@@ -259,6 +285,11 @@ __device__ __forceinline__ void key_pv(const EngineArgs& a, const GroupDev& G, c
 
 __device__ __forceinline__ bool pruned(i64 pv, u64 bound) {
     return bound != INF64 && pv >= 0 && (u64)pv >= bound;
+}
+
+template <int B>
+__device__ __forceinline__ PartnerDev partner(const EngineArgs& a, const Smem<B>& sm, u32 i, u32 p) {
+    return sm.pcached ? sm.pcache[sm.pbeg[i] + p] : a.partners[sm.pbeg[i] + p];
 }
 
 // mu[qe] <- min(mu[qe], s); on improvement refresh mumax of both ends (Table 2,
@@ -276,25 +307,27 @@ __device__ __forceinline__ void try_mu(const EngineArgs& a, const GroupDev& G, c
         u32 x = ends[k];
         u64 m = 0;
         for (u32 p = 0; p < sm.pcnt[x]; ++p) {
-            u64 mv = ldcg64(a.mu + a.partners[sm.pbeg[x] + p].qe);
+            u64 mv = ldcg64(a.mu + partner(a, sm, x, p).qe);
             m = mv > m ? mv : m;
         }
         amin64(a.mumax + G.sbeg + x, m);
     }
 }
 
-// UpdateDistance for <v, i> at distance d (bidirectional family)
+// UpdateDistance for <v, i> at distance d (bidirectional family, generic groups)
 template <typename D, int B>
 __device__ __forceinline__ void update_bidir(const EngineArgs& a, GCtx<D>& c, const Smem<B>& sm,
                                              u32 v, u32 i, u64 d) {
-    const u32 pb = sm.pbeg[i], pc = sm.pcnt[i];
+    const u32 pc = sm.pcnt[i];
     for (u32 p = 0; p < pc; ++p) {
-        PartnerDev pd = a.partners[pb + p];
+        PartnerDev pd = partner(a, sm, i, p);
         u64 o = ld_dist(c.dist + flat_of(c.G, c.n, v, pd.j));
         if (o != DT<D>::INF) try_mu(a, c.G, sm, pd.qe, d + o);
     }
 }
 
+// F.Add(<v, i>): dedup through the next-step bitmap; new entries are staged
+// in shared memory and appended to the global queue once per tile.
 template <typename D, int B>
 __device__ __forceinline__ void insert(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 f, u32 i,
                                        i64 key) {
@@ -303,15 +336,81 @@ __device__ __forceinline__ void insert(const EngineArgs& a, GCtx<D>& c, Smem<B>&
     if (!(old & bit)) {
         ++c.c_p;
         if (c.G.scnt == 2) atomicAdd(&sm.cnt_dir[i], 1u);
-        u32 pos = agg_inc(&c.S_nxt->count);
-        if (!c.dense_nxt) {
+        u32 s = atomicAdd(&sm.qn, 1u);
+        if (s < QSTAGE) {
+            sm.qbuf[s] = f;
+        } else {  // staging full: append directly
+            u32 pos = agg_inc(&c.S_nxt->count);
+            if (!c.dense_nxt) {
+                if (pos < c.slot.qcap)
+                    c.q_nxt[pos] = f;
+                else
+                    c.S_nxt->overflow = 1u;
+            }
+        }
+    }
+    atomicMin(reinterpret_cast<unsigned long long*>(&sm.minkey_acc), (unsigned long long)key);
+}
+
+template <typename D, int B>
+__device__ __forceinline__ void touch(GCtx<D>& c, Smem<B>& sm, u32 f) {
+    ++c.c_t;
+    u32 s = atomicAdd(&sm.tn, 1u);
+    if (s < TSTAGE) {
+        sm.tbuf[s] = f;
+    } else {
+        u32 pos = agg_inc(&c.slot.st->touched_n);
+        if (pos < c.slot.tcap)
+            c.slot.touched[pos] = f;
+        else
+            c.slot.st->touched_overflow = 1u;
+    }
+}
+
+// Write the staged frontier and touched entries of this tile to global memory:
+// one atomicAdd per CTA for each list, then coalesced stores.
+template <typename D, int B>
+__device__ __forceinline__ void flush_stage(GCtx<D>& c, Smem<B>& sm) {
+    const u32 t = threadIdx.x;
+    __syncthreads();
+    const u32 nq = min(sm.qn, (u32)QSTAGE), nt = min(sm.tn, (u32)TSTAGE);
+    if (t == 0) {
+        sm.qbase = nq ? atomicAdd(&c.S_nxt->count, nq) : 0u;
+        sm.tbase = nt ? atomicAdd(&c.slot.st->touched_n, nt) : 0u;
+    }
+    __syncthreads();
+    if (!c.dense_nxt) {
+        for (u32 k = t; k < nq; k += B) {
+            const u32 pos = sm.qbase + k;
             if (pos < c.slot.qcap)
-                c.q_nxt[pos] = f;
+                c.q_nxt[pos] = sm.qbuf[k];
             else
                 c.S_nxt->overflow = 1u;
         }
     }
-    atomicMin(reinterpret_cast<unsigned long long*>(&sm.minkey), (unsigned long long)key);
+    for (u32 k = t; k < nt; k += B) {
+        const u32 pos = sm.tbase + k;
+        if (pos < c.slot.tcap)
+            c.slot.touched[pos] = sm.tbuf[k];
+        else
+            c.slot.st->touched_overflow = 1u;
+    }
+    __syncthreads();
+    if (t == 0) {
+        sm.qn = 0;
+        sm.tn = 0;
+    }
+    __syncthreads();
+}
+
+// prune, then F.Add for a successful relaxation of <v2, i> to nd
+template <typename D, int B>
+__device__ __forceinline__ void after_relax(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 f2,
+                                            u32 i, int2 pv2, u64 nd) {
+    i64 key, pv;
+    key_pv<B>(a, c.G, sm, i, pv2, nd, key, pv);
+    if (pruned(pv, sm.bound[i])) return;
+    insert<D, B>(a, c, sm, f2, i, key);
 }
 
 template <typename D, int B>
@@ -319,37 +418,43 @@ __device__ __forceinline__ void relax(const EngineArgs& a, GCtx<D>& c, Smem<B>& 
                                       uint2 ew) {
     const u32 v2 = ew.x;
     const u64 nd = d + (u64)ew.y;
+    int2 pv2 = make_int2(0, 0);
+    if (sm.pot_any) pv2 = __ldg(a.g.pc + v2);  // prefetch, overlaps the distance load
     if (nd > DT<D>::MAXV) {
         atomicOr(a.err, ERRB_OVERFLOW);
         return;
     }
+    if (c.pair) {
+        u64 x0, x1;
+        ld_pair(c.dist, v2, x0, x1);
+        const u64 own = i ? x1 : x0, oth = i ? x0 : x1;
+        if (nd >= own) return;
+        const u32 f2 = (v2 << 1) | i;
+        const u64 old = amin_dist(c.dist + f2, nd);
+        if (nd >= old) return;
+        ++c.c_r;
+        if (old == DT<D>::INF) touch<D, B>(c, sm, f2);
+        if (oth != DT<D>::INF) try_mu(a, c.G, sm, c.G.qbeg, nd + oth);
+        after_relax<D, B>(a, c, sm, f2, i, pv2, nd);
+        return;
+    }
     const u32 f2 = flat_of(c.G, c.n, v2, i);
     if (nd >= ld_dist(c.dist + f2)) return;
-    u64 old = amin_dist(c.dist + f2, nd);
+    const u64 old = amin_dist(c.dist + f2, nd);
     if (nd >= old) return;
     ++c.c_r;
-    if (old == DT<D>::INF) {
-        ++c.c_t;
-        u32 pos = agg_inc(&c.slot.st->touched_n);
-        if (pos < c.slot.tcap)
-            c.slot.touched[pos] = f2;
-        else
-            c.slot.st->touched_overflow = 1u;
-    }
+    if (old == DT<D>::INF) touch<D, B>(c, sm, f2);
     if (c.G.mode == GM_BIDIR) {
         update_bidir<D, B>(a, c, sm, v2, i, nd);
     } else if (c.G.mode != GM_SSSP && v2 == c.G.target) {
         try_mu(a, c.G, sm, c.G.qbeg, nd);
     }
-    i64 key, pv;
-    key_pv<B>(a, c.G, sm, i, v2, nd, key, pv);
-    if (pruned(pv, sm.bound[i])) return;
-    insert<D, B>(a, c, sm, f2, i, key);
+    after_relax<D, B>(a, c, sm, f2, i, pv2, nd);
 }
 
 // Process sm.flat[0 .. cnt): extract, update, prune, then relax all edges of
 // the survivors with a load-balanced sweep (consecutive threads read
-// consecutive adjacency entries).
+// consecutive adjacency entries, 8 bytes each: target and weight).
 template <typename D, int B>
 __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 cnt, bool sparse_src,
                               u32* bm_cur) {
@@ -371,20 +476,35 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
         const u32 f = sm.flat[t];
         u32 v, i;
         decode_flat(c.G, c.n, f, v, i);
+        // independent loads issued together: offsets, potential coordinates, distances
+        const u32 b0 = __ldg(a.g.off + v);
+        const u32 b1 = __ldg(a.g.off + v + 1);
+        int2 pv2 = make_int2(0, 0);
+        if (sm.pot_any) pv2 = __ldg(a.g.pc + v);
         if (sparse_src) atomicAnd(bm_cur + (f >> 5), ~(1u << (f & 31u)));
-        const u64 d = ld_dist(c.dist + f);
+        u64 d, oth = DT<D>::INF;
+        if (c.pair) {
+            u64 x0, x1;
+            ld_pair(c.dist, v, x0, x1);
+            d = i ? x1 : x0;
+            oth = i ? x0 : x1;
+        } else {
+            d = ld_dist(c.dist + f);
+        }
         if (d != DT<D>::INF) {
             i64 key, pv;
-            key_pv<B>(a, c.G, sm, i, v, d, key, pv);
+            key_pv<B>(a, c.G, sm, i, pv2, d, key, pv);
             if ((u64)key > c.theta) {
                 insert<D, B>(a, c, sm, f, i, key);  // stays in F
             } else {
-                if (c.G.mode == GM_BIDIR) update_bidir<D, B>(a, c, sm, v, i, d);
+                if (c.pair) {
+                    if (oth != DT<D>::INF) try_mu(a, c.G, sm, c.G.qbeg, d + oth);
+                } else if (c.G.mode == GM_BIDIR) {
+                    update_bidir<D, B>(a, c, sm, v, i, d);
+                }
                 if (!pruned(pv, sm.bound[i])) {
-                    const u32 b0 = __ldg(a.g.off + v);
-                    deg = __ldg(a.g.off + v + 1) - b0;
+                    deg = b1 - b0;
                     sm.beg[t] = b0;
-                    sm.v[t] = v;
                     sm.si[t] = (unsigned char)i;
                     sm.d[t] = d;
                     ++c.c_x;
@@ -407,7 +527,7 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
         ++c.c_e;
         relax<D, B>(a, c, sm, sm.si[lo], sm.d[lo], ew);
     }
-    __syncthreads();
+    flush_stage<D, B>(c, sm);
 }
 
 // ----------------------------------------------------------------------------
@@ -425,19 +545,39 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
     c.c_x = c.c_e = c.c_r = c.c_p = c.c_t = 0;
     const GroupDev& G = c.G;
     StepState* S = slot.st->s;
+    const u64 t_start = (a.group_ns && tc.rank == 0 && t == 0) ? global_ns() : 0;
 
     // group cache
+    c.pair = (G.mode == GM_BIDIR && G.scnt == 2 && G.layout == PPSP_LAYOUT_INTERLEAVED && G.kshift == 1);
+    if (t == 0) {
+        const SearchDev s0 = a.searches[G.sbeg];
+        const SearchDev sl = a.searches[G.sbeg + G.scnt - 1];
+        const u32 np = sl.pbeg + sl.pcnt - s0.pbeg;
+        sm.pcached = (np <= PCAP) ? 1u : 0u;
+        sm.pot_any = (G.mode == GM_ASTAR) ? 1u : 0u;
+        sm.qn = 0;
+        sm.tn = 0;
+    }
+    __syncthreads();
     if (t < G.scnt) {
         SearchDev s = a.searches[G.sbeg + t];
+        const u32 p0 = a.searches[G.sbeg].pbeg;
         sm.src[t] = s.src;
-        sm.pbeg[t] = s.pbeg;
+        sm.pbeg[t] = sm.pcached ? s.pbeg - p0 : s.pbeg;
         sm.pcnt[t] = s.pcnt;
         sm.pot[t] = s.pot;
         sm.key_off[t] = s.key_off;
+        if (s.pot) atomicOr(&sm.pot_any, 1u);
         if (a.g.pc != nullptr) {
             sm.pa[t] = a.g.pc[s.src];
             sm.pb[t] = a.g.pc[s.pot_b];
         }
+    }
+    if (sm.pcached) {
+        const SearchDev s0 = a.searches[G.sbeg];
+        const SearchDev sl = a.searches[G.sbeg + G.scnt - 1];
+        const u32 np = sl.pbeg + sl.pcnt - s0.pbeg;
+        for (u32 k = t; k < np; k += B) sm.pcache[k] = a.partners[s0.pbeg + k];
     }
     __syncthreads();
 
@@ -481,7 +621,7 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
         if (t < G.scnt && G.mode == GM_BIDIR) {
             u64 m = 0;
             for (u32 p = 0; p < sm.pcnt[t]; ++p) {
-                u64 mv = a.mu[a.partners[sm.pbeg[t] + p].qe];
+                u64 mv = a.mu[partner(a, sm, t, p).qe];
                 m = mv > m ? mv : m;
             }
             a.mumax[G.sbeg + t] = (sm.pcnt[t] == 0) ? INF64 : m;
@@ -505,14 +645,14 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
         if (t == 0) {
             sm.count = ld_volatile(&S[cur].count);
             sm.overflow = ld_volatile(&S[cur].overflow);
-            sm.minkey = ldcg64(&S[cur].minkey);
+            sm.minkey_in = ldcg64(&S[cur].minkey);
             sm.dir0 = ld_volatile(&S[cur].cnt_dir[0]);
             sm.dir1 = ld_volatile(&S[cur].cnt_dir[1]);
             sm.mu0 = ldcg64(a.mu + G.qbeg);
         }
         __syncthreads();
         const u32 count = sm.count;
-        const u64 minkey = sm.minkey;
+        const u64 minkey = sm.minkey_in;
         dense_cur = dense_cur || sm.overflow != 0;
         bool stop = (count == 0);
         // App. B: a two-search group whose one side ran dry before mu was ever
@@ -548,7 +688,7 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
             S[old].cnt_dir[0] = S[old].cnt_dir[1] = 0;
         }
         if (t == 0) {
-            sm.minkey = INF64;
+            sm.minkey_acc = INF64;
             sm.cnt_dir[0] = sm.cnt_dir[1] = 0;
         }
         __syncthreads();
@@ -604,8 +744,8 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
         // flush per-CTA step results
         __syncthreads();
         if (t == 0) {
-            if (sm.minkey != INF64)
-                amin64(&S[nxt].minkey, sm.minkey);
+            if (sm.minkey_acc != INF64)
+                amin64(&S[nxt].minkey, sm.minkey_acc);
             if (sm.cnt_dir[0]) atomicAdd(&S[nxt].cnt_dir[0], sm.cnt_dir[0]);
             if (sm.cnt_dir[1]) atomicAdd(&S[nxt].cnt_dir[1], sm.cnt_dir[1]);
         }
@@ -641,6 +781,7 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
     cnt_acc[2] += c.c_r;
     cnt_acc[3] += c.c_p;
     cnt_acc[7] += c.c_t;
+    if (a.group_ns && t == 0 && tc.rank == 0) a.group_ns[gi] = global_ns() - t_start;
     if (t == 0 && tc.rank == 0) {
         cnt_acc[4] += rounds;
         cnt_acc[5] += 1;

@@ -53,6 +53,8 @@ struct ppsp_graph {
     ppsp::u32* d_scratch_u32 = nullptr;
     int64_t* d_scratch_i64 = nullptr;
     uint64_t scratch_cap = 0;
+    // learned stepping-increment models, one per plug-in (borrowed)
+    ppsp_delta_model* delta_model[4] = {nullptr, nullptr, nullptr, nullptr};
 
     ppsp::GraphDev dev() const {
         ppsp::GraphDev g;

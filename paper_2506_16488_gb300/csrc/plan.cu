@@ -6,6 +6,7 @@
 #include <unordered_map>
 
 #include "graph_impl.h"
+#include "mlp_internal.h"
 
 using namespace ppsp;
 
@@ -33,6 +34,11 @@ struct ppsp_plan {
     u32* d_map = nullptr;
     EngineArgs args{};
     bool launched = false;
+    // learned Delta: per-group features (log2(1 + raw)) and the model used
+    std::vector<float> feats;
+    float* d_feats = nullptr;
+    ppsp_delta_model* model = nullptr;
+    u64 delta_default = 1;
 };
 
 namespace {
@@ -262,6 +268,38 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     for (u64 q = 0; q < k; ++q)
         if (P->map[q] != NONE) P->map[q] = uq_to_qe[P->map[q]];
 
+    // ---- features of the learned stepping increment (per group) ----
+    // raw: heuristic distance, deg(s), deg(t), w mean/std/min/max, n, m,
+    // |V_q|, |E_q|, mean query-graph degree; the model sees log2(1 + raw).
+    P->delta_default = delta;
+    P->feats.assign((size_t)NG * 12, 0.f);
+    for (u32 gi = 0; gi < NG; ++gi) {
+        const GroupDev& G = P->groups[gi];
+        double hsum = 0.0;
+        for (u32 qi = 0; qi < G.qcnt; ++qi) {
+            auto ends = P->qedge_ends[G.qbeg + qi];
+            if (g->info.has_coords) hsum += (double)pot_h_host(g, ends.first, ends.second);
+        }
+        double dmean = 0.0, dmax = 0.0;
+        for (u32 i = 0; i < G.scnt; ++i) {
+            double d = (double)g->deg[P->searches[G.sbeg + i].src];
+            dmean += d / G.scnt;
+            dmax = std::max(dmax, d);
+        }
+        double ds = (double)g->deg[P->searches[G.sbeg].src];
+        double dt = G.scnt >= 2 ? (double)g->deg[P->searches[G.sbeg + 1].src]
+                                : (G.target != NONE ? (double)g->deg[G.target] : 0.0);
+        if (G.scnt > 2) {
+            ds = dmean;
+            dt = dmax;
+        }
+        const double raw[12] = {hsum / std::max<u32>(1, G.qcnt), ds, dt, g->info.w_mean, g->info.w_std,
+                                (double)g->info.w_min, (double)g->info.w_max, (double)g->n, (double)g->m,
+                                (double)G.scnt, (double)G.qcnt, 2.0 * G.qcnt / std::max<u32>(1, G.scnt)};
+        for (int f = 0; f < 12; ++f) P->feats[(size_t)gi * 12 + f] = (float)std::log2(1.0 + std::max(0.0, raw[f]));
+    }
+    if (o.delta == 0 && g->delta_model[o.mode] != nullptr) P->model = g->delta_model[o.mode];
+
     // ---- launch shape ----
     int block = o.block_threads ? o.block_threads : 512;
     int bpsm = 0, sms = 0;
@@ -307,7 +345,10 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         }
         u32 g_small = grid - nbt * tb;
         if (!small.empty() && g_small > 0) {
-            u32 ts = o.team_ctas ? std::min<u32>((u32)o.team_ctas, g_small) : 1;
+            // fewer groups than CTAs: give each group a team of several CTAs
+            u32 ts_auto = 1;
+            while (ts_auto * 2 <= 32 && (u64)ts_auto * 2 * small.size() <= g_small) ts_auto *= 2;
+            u32 ts = o.team_ctas ? std::min<u32>((u32)o.team_ctas, g_small) : ts_auto;
             u32 nst = std::max<u32>(1, g_small / ts);
             for (u32 t = 0; t < nst; ++t) teams.push_back({ts, 1});
             g_small = nst * ts;
@@ -373,6 +414,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     size_t o_slots = take(NT * sizeof(SlotDev));
     size_t o_q0 = take(P->queue_items[0].size() * 4), o_q1 = take(P->queue_items[1].size() * 4);
     size_t o_map = take(k * 4);
+    size_t o_feat = take(P->feats.size() * 4);
     size_t static_bytes = off;
     size_t o_mu = take(P->qedges.size() * 8);
     size_t o_mumax = take(P->searches.size() * 8);
@@ -381,6 +423,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     size_t o_ts = take(NT * sizeof(TeamState));
     size_t o_err = take(4);
     size_t o_cnt = take(sizeof(EngineCounters));
+    size_t o_gns = take(P->groups.size() * 8);
     P->runstate_bytes = off - o_run;
     P->arena_bytes = off;
     cudaError_t ce = cudaMalloc(&P->d_arena, P->arena_bytes);
@@ -408,6 +451,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     put(o_q0, P->queue_items[0].data(), P->queue_items[0].size() * 4);
     put(o_q1, P->queue_items[1].data(), P->queue_items[1].size() * 4);
     put(o_map, P->map.data(), k * 4);
+    put(o_feat, P->feats.data(), P->feats.size() * 4);
     ce = cudaMemcpy(base, h.data(), static_bytes, cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) {
         cudaGetLastError();
@@ -439,8 +483,10 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     a.spin_limit = o.spin_limit ? o.spin_limit : (1ull << 26);
     a.err = (u32*)(base + o_err);
     a.counters = (EngineCounters*)(base + o_cnt);
+    a.group_ns = (u64*)(base + o_gns);
     P->d_runstate = base + o_run;
     P->d_map = (u32*)(base + o_map);
+    P->d_feats = (float*)(base + o_feat);
     *out = P.release();
     return PPSP_OK;
 }
@@ -461,6 +507,12 @@ static ppsp_status plan_launch(ppsp_plan* P, u64* d_out) {
     ppsp_status st = pool_scrub(P->g, P->stream);
     if (st != PPSP_OK) return st;
     PPSP_CUDA_TRY(cudaMemsetAsync(P->d_runstate, 0, P->runstate_bytes, P->stream));
+    if (P->model && !P->groups.empty()) {
+        // learned Delta per group, written into the device group descriptors
+        st = mlp_launch_infer(P->model, P->d_feats, P->groups.size(), nullptr, const_cast<GroupDev*>(P->args.groups),
+                              P->delta_default, P->stream);
+        if (st != PPSP_OK) return st;
+    }
     if (!P->groups.empty()) {
         st = launch_engine(P->args, P->dist_bits, P->block, P->grid, P->stream);
         if (st != PPSP_OK) return st;
@@ -525,6 +577,33 @@ ppsp_status ppsp_plan_sync(ppsp_plan* p, ppsp_counters* counters) {
     if (!p->launched) return PPSP_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(p->g->mu);
     return plan_wait(p, counters);
+}
+
+ppsp_status ppsp_plan_features(const ppsp_plan* p, float* out, uint64_t cap, uint64_t* ngroups) {
+    if (!p || !ngroups) return PPSP_ERR_INVALID_ARG;
+    *ngroups = p->groups.size();
+    if (out) {
+        if (cap < p->groups.size()) return PPSP_ERR_BUFFER_TOO_SMALL;
+        memcpy(out, p->feats.data(), p->feats.size() * 4);
+    }
+    return PPSP_OK;
+}
+
+ppsp_status ppsp_plan_group_times(ppsp_plan* p, uint64_t* out_ns, uint64_t cap, uint64_t* ngroups) {
+    if (!p || !ngroups) return PPSP_ERR_INVALID_ARG;
+    *ngroups = p->groups.size();
+    if (!out_ns) return PPSP_OK;
+    if (cap < p->groups.size()) return PPSP_ERR_BUFFER_TOO_SMALL;
+    if (!p->launched) return PPSP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(p->g->mu);
+    if (p->stream) {
+        PPSP_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    } else {
+        PPSP_CUDA_TRY(cudaDeviceSynchronize());
+    }
+    if (!p->groups.empty())
+        PPSP_CUDA_TRY(cudaMemcpy(out_ns, p->args.group_ns, p->groups.size() * 8, cudaMemcpyDeviceToHost));
+    return PPSP_OK;
 }
 
 void ppsp_plan_destroy(ppsp_plan* p) {

@@ -138,6 +138,7 @@ struct EngineArgs {
     u64 spin_limit;
     u32* err;
     EngineCounters* counters;
+    u64* group_ns;        // [groups] device time of each group, or null
 };
 
 // ---- host helpers shared between translation units ----

@@ -1,0 +1,183 @@
+"""Learned stepping increment: sweep labels, train the MLP on the GPU, judge regret.
+
+The paper picks Delta for Delta*-stepping by doubling it until the geometric
+mean time stops improving (Sec. 7.1).  Here the same sweep produces training
+labels: every group of a batch is timed on the device (ppsp_plan_group_times)
+for Delta = Delta_default * 2^j over a grid of j, and its label is the j of
+its fastest run.  The model (12 -> 64 -> 64 -> 1, ppsp_delta_model_*) is
+trained with the library's own Adam kernel; its regret is the total group
+time at the predicted grid point over the total at each group's best grid
+point, minus one.  Delta never changes an answer (Theorems 4.1/4.2), so a bad
+prediction costs time only; without a model the library uses Delta_default
+(mean edge weight).
+
+Weights are stored as a flat float32 file plus a JSON file of metadata.
+"""
+
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import numpy as np
+
+from . import ppsp
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+WEIGHTS_DIR = os.path.join(HERE, "weights")
+GRID = tuple(range(-6, 3))  # log2(Delta / Delta_default)
+
+
+def weights_path(mode: str) -> str:
+    return os.path.join(WEIGHTS_DIR, f"delta_{mode}.bin")
+
+
+def sweep(G: ppsp.Graph, pairs: np.ndarray, mode: str, grid=GRID, stream=None, reps: int = 1, **opts):
+    """Time every group of the batch at each grid point.
+
+    Returns (features [groups, 12], times_ns [groups, len(grid)], default_delta).
+    """
+    import torch
+
+    default = max(1, int(round(G.info()["w_mean"])))
+    s = stream or torch.cuda.Stream()
+    out = torch.zeros(pairs.shape[0], dtype=torch.int64, device="cuda")
+    feats, times, ref = None, [], None
+    for j in grid:
+        delta = max(1, int(round(default * 2.0 ** j)))
+        plan = G.plan(pairs, mode=mode, delta=delta, stream=s.cuda_stream, **opts)
+        if feats is None:
+            feats = plan.features()
+        best = None
+        for _ in range(reps + 1):  # first run warms up
+            plan.run(out.data_ptr())
+            plan.sync()
+            t = plan.group_times().astype(np.float64)
+            best = t if best is None else np.minimum(best, t)
+        res = out.cpu().numpy().copy()
+        if ref is None:
+            ref = res
+        elif not np.array_equal(ref, res):  # Delta must not change answers
+            raise AssertionError(f"answers changed with delta={delta}")
+        times.append(best)
+        plan.close()
+    return feats, np.stack(times, axis=1), default
+
+
+def labels_from_times(times: np.ndarray, grid=GRID) -> np.ndarray:
+    return np.asarray(grid, dtype=np.float32)[np.argmin(times, axis=1)]
+
+
+def regret(times: np.ndarray, y_pred: np.ndarray, grid=GRID) -> float:
+    g = np.asarray(grid, dtype=np.float64)
+    idx = np.abs(np.clip(y_pred, g[0], g[-1])[:, None] - g[None, :]).argmin(axis=1)
+    chosen = times[np.arange(times.shape[0]), idx].sum()
+    return float(chosen / times.min(axis=1).sum() - 1.0)
+
+
+def default_regret(times: np.ndarray, grid=GRID) -> float:
+    j0 = list(grid).index(0)
+    return float(times[:, j0].sum() / times.min(axis=1).sum() - 1.0)
+
+
+def init_params(feats: np.ndarray, seed: int = 0) -> np.ndarray:
+    """Standardisation from the training features; He-normal weights."""
+    rng = np.random.default_rng(seed)
+    mean = feats.mean(axis=0)
+    std = feats.std(axis=0)
+    std = np.where(std < 1e-3, 1.0, std)
+    parts = [mean, std,
+             rng.normal(scale=np.sqrt(2.0 / 12), size=64 * 12), np.zeros(64),
+             rng.normal(scale=np.sqrt(2.0 / 64), size=64 * 64), np.zeros(64),
+             rng.normal(scale=np.sqrt(1.0 / 64), size=64), np.zeros(1)]
+    p = np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in parts]).astype(np.float32)
+    assert p.shape == (ppsp.MLP_PARAMS,)
+    return p
+
+
+def train(feats: np.ndarray, labels: np.ndarray, epochs: int = 600, lr: float = 3e-3, seed: int = 0):
+    model = ppsp.DeltaModel(init_params(feats, seed))
+    loss = model.train(feats, labels, epochs, lr)
+    return model, loss
+
+
+def save(model: ppsp.DeltaModel, mode: str, meta: dict, directory: str = WEIGHTS_DIR) -> str:
+    os.makedirs(directory, exist_ok=True)
+    path = os.path.join(directory, f"delta_{mode}.bin")
+    model.params().astype("<f4").tofile(path)
+    with open(path[:-4] + ".json", "w") as f:
+        json.dump(meta, f, indent=1, sort_keys=True)
+    return path
+
+
+def load_model(mode: str, directory: str = WEIGHTS_DIR):
+    path = os.path.join(directory, f"delta_{mode}.bin")
+    if not os.path.exists(path):
+        return None
+    p = np.fromfile(path, dtype="<f4")
+    if p.shape != (ppsp.MLP_PARAMS,):
+        return None
+    return ppsp.DeltaModel(p)
+
+
+def _training_sets(mode: str):
+    """Query sets used for training: held-out seeds, several graph shapes."""
+    from workloads import near_mid_far_pairs, random_pairs, rmat_graph, road_like_graph, grid_graph, clique_pairs
+
+    sets = []
+    g = road_like_graph(1024, seed=2001)  # the road-like benchmark graph, other queries
+    p, _ = near_mid_far_pairs(g, 1000, seed=2777)
+    sets.append(("road1024", g, p))
+    g = road_like_graph(512, seed=9001)
+    p, _ = near_mid_far_pairs(g, 600, seed=9002)
+    sets.append(("road512", g, np.concatenate([p, clique_pairs(g, 12, 9003)])))
+    g = grid_graph(64, seed=9101)
+    sets.append(("grid64", g, random_pairs(g, 300, 9102)))
+    if mode == "bids":
+        g = rmat_graph(18, seed=9201)
+        sets.append(("rmat18", g, random_pairs(g, 128, 9202)))
+    return sets
+
+
+def build_and_train(mode: str, out_dir: str = WEIGHTS_DIR, epochs: int = 600, log=print) -> dict:
+    """Sweep Delta on the training sets, train, report regret, save weights."""
+    feats_all, labels_all, meta_sets = [], [], []
+    t0 = time.time()
+    for name, g, pairs in _training_sets(mode):
+        with ppsp.Graph.from_csr(g, with_coords=g.coords is not None) as G:
+            m = mode if (mode != "bidastar" or g.coords is not None) else "bids"
+            feats, times, default = sweep(G, pairs, m)
+        lab = labels_from_times(times)
+        feats_all.append(feats)
+        labels_all.append(lab)
+        meta_sets.append({"set": name, "groups": int(feats.shape[0]), "default_delta": default,
+                          "default_regret": default_regret(times),
+                          "label_hist": {str(j): int((lab == j).sum()) for j in GRID}})
+        log(json.dumps(meta_sets[-1]))
+    F = np.concatenate(feats_all)
+    Y = np.concatenate(labels_all)
+    model, loss = train(F, Y, epochs=epochs)
+    pred = model.predict(F)
+    meta = {"mode": mode, "grid": list(GRID), "epochs": epochs, "train_loss": loss,
+            "train_groups": int(F.shape[0]), "sets": meta_sets, "seconds": time.time() - t0,
+            "features": "log2(1 + raw): h(s,t), deg(s), deg(t), w mean/std/min/max, n, m, |V_q|, |E_q|, "
+                        "mean query-graph degree",
+            "train_mae": float(np.abs(pred - Y).mean())}
+    path = save(model, mode, meta, out_dir)
+    log(json.dumps({"saved": path, "train_loss": loss, "train_mae": meta["train_mae"]}))
+    model.close()
+    return meta
+
+
+if __name__ == "__main__":
+    import sys
+
+    root = os.path.dirname(HERE)
+    sys.path.insert(0, root)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    modes = sys.argv[1:] or ["bidastar", "bids"]
+    for md in modes:
+        build_and_train(md)

@@ -31,6 +31,8 @@ LAYOUT = {"auto": 0, "interleaved": 1, "stacked": 2}
 STRATEGY = {"multi": 0, "plain_star": 1, "plain": 2}
 UNDIRECTED = 1
 DEBUG_BARRIER_NEVER_RELEASES = 1
+MLP_FEATURES = 12
+MLP_PARAMS = 5081
 
 
 class Options(ctypes.Structure):
@@ -124,6 +126,15 @@ def load(build_if_missing: bool = False):
             "ppsp_plan_destroy": (None, [p]),
             "ppsp_potential_coords": (S, [p, p]),
             "ppsp_potential_eval": (S, [p, u32, p, u64, p]),
+            "ppsp_plan_features": (S, [p, p, u64, p]),
+            "ppsp_plan_group_times": (S, [p, p, u64, p]),
+            "ppsp_delta_model_create": (S, [p, p]),
+            "ppsp_delta_model_destroy": (None, [p]),
+            "ppsp_delta_model_get_params": (S, [p, p]),
+            "ppsp_delta_model_predict": (S, [p, p, u64, p]),
+            "ppsp_delta_model_grad": (S, [p, p, p, u64, p, p]),
+            "ppsp_delta_model_train": (S, [p, p, p, u64, u32, ctypes.c_float, p]),
+            "ppsp_graph_set_delta_model": (S, [p, i32, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -251,6 +262,15 @@ class Graph:
     def plan(self, pairs, **opts) -> "Plan":
         return Plan(self, pairs, **opts)
 
+    def set_delta_model(self, mode: str | int, model: Optional["DeltaModel"]):
+        """Plans of this mode with delta=0 use the model (kept alive by the graph)."""
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        _check(load().ppsp_graph_set_delta_model(self._h, m, model._h if model else None),
+               "ppsp_graph_set_delta_model")
+        if not hasattr(self, "_models"):
+            self._models = {}
+        self._models[m] = model
+
     def potential_coords(self) -> np.ndarray:
         out = np.empty(2 * self.n, dtype=np.int64)
         _check(load().ppsp_potential_coords(self._h, _ptr(out)), "ppsp_potential_coords")
@@ -285,9 +305,77 @@ class Plan:
         _check(load().ppsp_plan_sync(self._h, ctypes.byref(c)), "ppsp_plan_sync")
         return c.as_dict()
 
+    def features(self) -> np.ndarray:
+        """Per-group model features, float32 [groups, 12]."""
+        ng = ctypes.c_uint64(0)
+        _check(load().ppsp_plan_features(self._h, None, 0, ctypes.byref(ng)), "ppsp_plan_features")
+        out = np.zeros((ng.value, MLP_FEATURES), dtype=np.float32)
+        _check(load().ppsp_plan_features(self._h, _ptr(out), ng.value, ctypes.byref(ng)), "ppsp_plan_features")
+        return out
+
+    def group_times(self) -> np.ndarray:
+        """Device ns per group of the last run, uint64 [groups]."""
+        ng = ctypes.c_uint64(0)
+        _check(load().ppsp_plan_group_times(self._h, None, 0, ctypes.byref(ng)), "ppsp_plan_group_times")
+        out = np.zeros(ng.value, dtype=np.uint64)
+        _check(load().ppsp_plan_group_times(self._h, _ptr(out), ng.value, ctypes.byref(ng)),
+               "ppsp_plan_group_times")
+        return out
+
     def close(self):
         if getattr(self, "_h", None):
             load().ppsp_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DeltaModel:
+    """The stepping-increment MLP on the device (ppsp_delta_model_*)."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.shape == (MLP_PARAMS,)
+        h = ctypes.c_void_p()
+        _check(load().ppsp_delta_model_create(_ptr(p), ctypes.byref(h)), "ppsp_delta_model_create")
+        self._h = h
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, dtype=np.float32)
+        _check(load().ppsp_delta_model_get_params(self._h, _ptr(out)), "ppsp_delta_model_get_params")
+        return out
+
+    def predict(self, feats) -> np.ndarray:
+        f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MLP_FEATURES)
+        out = np.empty(f.shape[0], dtype=np.float32)
+        _check(load().ppsp_delta_model_predict(self._h, _ptr(f), f.shape[0], _ptr(out)),
+               "ppsp_delta_model_predict")
+        return out
+
+    def grad(self, feats, labels) -> tuple:
+        f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MLP_FEATURES)
+        y = np.ascontiguousarray(labels, dtype=np.float32)
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float(0)
+        _check(load().ppsp_delta_model_grad(self._h, _ptr(f), _ptr(y), f.shape[0], _ptr(g), ctypes.byref(loss)),
+               "ppsp_delta_model_grad")
+        return g, float(loss.value)
+
+    def train(self, feats, labels, epochs: int, lr: float) -> float:
+        f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MLP_FEATURES)
+        y = np.ascontiguousarray(labels, dtype=np.float32)
+        loss = ctypes.c_float(0)
+        _check(load().ppsp_delta_model_train(self._h, _ptr(f), _ptr(y), f.shape[0], epochs, lr,
+                                             ctypes.byref(loss)), "ppsp_delta_model_train")
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ppsp_delta_model_destroy(self._h)
             self._h = None
 
     def __del__(self):
