@@ -3,8 +3,8 @@
 Workload (default): the road-like 1024 x 1024 jittered grid (about 1.05 M
 vertices, 10% of grid edges deleted, 0.5% shortcuts of at most 20 cells,
 weights round(1000 * length)) with 1,000 queries split into near/mid/far
-thirds by grid distance, answered with bidirectional A* (Sec. 4.5) as one
-batch (Multi-BiDS schedule, Sec. 5.2).  A step is one pass of the whole batch.
+thirds by grid distance, answered with bidirectional A* (Sec. 3.5) as one
+batch (Multi-BiDS schedule, Sec. 4.2).  A step is one pass of the whole batch.
 
 Reported:
   value        queries/sec with the graph, the pairs and the output in HBM

@@ -5,10 +5,10 @@
  * with the paper's stepping-style PPSP framework (Alg. 2): a frontier is
  * processed in steps under an advancing threshold (Alg. 1, Delta*-stepping,
  * Sec. 2), with the Init / Prune / UpdateDistance plug-ins of Table 2 for
- * early termination (ET, Sec. 4.2), A* (Sec. 4.3), bidirectional search (BiDS,
- * Sec. 4.4, Theorem 4.1) and bidirectional A* (BiD-A*, Sec. 4.5, Theorem 4.2),
- * and batches of queries organised as a query graph (Sec. 5.1) and searched
- * with Multi-BiDS (Sec. 5.2).  All arithmetic on distances is integer, so
+ * early termination (ET, Sec. 3.2), A* (Sec. 3.3), bidirectional search (BiDS,
+ * Sec. 3.4, Theorem 3.3) and bidirectional A* (BiD-A*, Sec. 3.5, Theorem 3.4),
+ * and batches of queries organised as a query graph (Sec. 4.1) and searched
+ * with Multi-BiDS (Sec. 4.2).  All arithmetic on distances is integer, so
  * results are exact.  The paper defines no programming interface; names and
  * layouts here are this library's own.
  *
@@ -53,10 +53,10 @@ typedef enum {
 
 /* Search plug-ins (Table 2). */
 enum {
-    PPSP_BIDS = 0,     /* bidirectional search, prune 2*d >= mu (Sec. 4.4)            */
-    PPSP_BIDASTAR = 1, /* bidirectional A*, average potential h_F = -h_B (Sec. 4.5)   */
+    PPSP_BIDS = 0,     /* bidirectional search, prune 2*d >= mu (Sec. 3.4)            */
+    PPSP_BIDASTAR = 1, /* bidirectional A*, average potential h_F = -h_B (Sec. 3.5)   */
     PPSP_ET = 2,       /* one-directional with early termination, prune d >= mu       */
-    PPSP_ASTAR = 3     /* one-directional A*, prune d + h_t(v) >= mu (Sec. 4.3)       */
+    PPSP_ASTAR = 3     /* one-directional A*, prune d + h_t(v) >= mu (Sec. 3.3)       */
 };
 
 /* Graph flags. */
@@ -68,7 +68,7 @@ enum { PPSP_FRONTIER_AUTO = 0, PPSP_FRONTIER_SPARSE = 1, PPSP_FRONTIER_DENSE = 2
 /* Layout of the per-search tentative-distance arrays of one batch group. */
 enum { PPSP_LAYOUT_AUTO = 0, PPSP_LAYOUT_INTERLEAVED = 1, PPSP_LAYOUT_STACKED = 2 };
 
-/* How a batch is executed (Sec. 5.2 and the batch baselines of Sec. 7). */
+/* How a batch is executed (Sec. 4.2 and the batch baselines of Sec. 6). */
 enum {
     PPSP_BATCH_MULTI = 0,      /* Multi-BiDS: one search per query-graph vertex, shared  */
     PPSP_BATCH_PLAIN_STAR = 1, /* Plain*: every query its own pair of searches, all at once */
@@ -78,7 +78,7 @@ enum {
 /*
  * Query options.  Call ppsp_options_init() first; it fills in the defaults
  * noted beside each field.  Options never change answers, only speed
- * (Theorems 4.1 and 4.2 hold for any stepping schedule), except mode, which
+ * (Theorems 3.3 and 3.4 hold for any stepping schedule), except mode, which
  * selects the plug-in, and dist_bits, which bounds representable distances.
  */
 typedef struct {
@@ -106,7 +106,7 @@ typedef struct {
  * multi-CTA wait runs out and the call returns PPSP_ERR_TIMEOUT. */
 #define PPSP_DEBUG_BARRIER_NEVER_RELEASES 1u
 
-/* Work counters of one call (paper Sec. 7 measures time; these feed GTEPS and
+/* Work counters of one call (paper Sec. 6 measures time; these feed GTEPS and
  * the algorithmic-bytes roofline). */
 typedef struct {
     uint64_t extracted;   /* frontier entries taken and not pruned (X)           */
@@ -173,7 +173,7 @@ ppsp_status ppsp_graph_get_info(const ppsp_graph* g, ppsp_graph_info* out);
 
 /*
  * One query d(s, t) with the plug-in of opt->mode (NULL opt = defaults), on
- * the whole GPU ("Plain" execution of one query, Sec. 5.2).
+ * the whole GPU ("Plain" execution of one query, Sec. 4.2).
  *   dist_out  host uint64, receives d(s, t) or PPSP_INF
  *   path_buf  host uint32[path_cap] or NULL; with opt->want_paths it receives
  *             one shortest path s..t (s == t gives [s])
@@ -189,8 +189,8 @@ ppsp_status ppsp_query(ppsp_graph* g, uint32_t s, uint32_t t, const ppsp_options
                        uint64_t* path_len);
 
 /*
- * A batch of k queries (Sec. 5): pairs is host uint32[2k] (s0, t0, s1, t1, ...).
- * The batch is turned into a query graph G_q (Sec. 5.1; repeated and reversed
+ * A batch of k queries (Sec. 4): pairs is host uint32[2k] (s0, t0, s1, t1, ...).
+ * The batch is turned into a query graph G_q (Sec. 4.1; repeated and reversed
  * pairs collapse to one query edge) and run with opt->batch_strategy.
  *   dists_out     host uint64[k], answer of each pair in input order
  *   paths_buf     host uint32 buffer or NULL (needs opt->want_paths)
@@ -222,7 +222,7 @@ ppsp_status ppsp_plan_sync(ppsp_plan* p, ppsp_counters* counters);
 void ppsp_plan_destroy(ppsp_plan* p);
 
 /*
- * A* potential of the graph (Sec. 4.3; consistency, Fact 4.1).  The library
+ * A* potential of the graph (Sec. 3.3; consistency, Fact 3.1).  The library
  * stores integer potential coordinates P(v) = floor(p(v) * c * 2^F + 0.5)
  * (float64 arithmetic, c and F in ppsp_graph_info) chosen at creation so that
  * |P(u) - P(v)|^2 <= (2^F * w(u,v))^2 on every edge; the potential is
@@ -258,8 +258,8 @@ ppsp_status ppsp_plan_group_times(ppsp_plan* p, uint64_t* out_ns, uint64_t cap, 
 
 /*
  * Learned stepping increment.  The paper tunes Delta of Delta*-stepping by
- * doubling it until the time stops improving (Sec. 7.1); Delta changes only
- * the schedule, never an answer (Theorems 4.1/4.2).  This library predicts it
+ * doubling it until the time stops improving (Sec. 6.1); Delta changes only
+ * the schedule, never an answer (Theorems 3.3/3.4).  This library predicts it
  * per group with a 12 -> 64 -> 64 -> 1 MLP (ReLU; bf16 weights, fp32
  * accumulation): y = log2(Delta / Delta_default), Delta_default = mean edge
  * weight, Delta = round(Delta_default * 2^clamp(y, -8, 6)), at least 1.

@@ -5,10 +5,10 @@ leg import this package.  It shares no code with the CUDA path
 (``paper_2506_16488_gb300``) and never imports it.
 
 * ``ppsp_oracle.c`` -- binary-heap Dijkstra (the plain definition of d(s,t),
-  which Theorems 4.1/4.2 say BiDS and BiD-A* return exactly), full SSSP with
+  which Theorems 3.3/3.4 say BiDS and BiD-A* return exactly), full SSSP with
   parents, Floyd-Warshall for tiny graphs.
 * ``potential.py`` -- the integer A* potential h_x(v) = floor(scaled Euclidean
-  distance) (Sec. 4.3; Fact 4.1 consistency).
+  distance) (Sec. 3.3; Fact 3.1 consistency).
 * ``mlp.py`` -- float64 forward/backward of the small stepping-threshold MLP.
 """
 

@@ -1,8 +1,8 @@
 """Float64 reference of the stepping-threshold MLP.  TEST INFRASTRUCTURE ONLY.
 
 The paper tunes Delta of Delta*-stepping by doubling until the time stops
-improving (Sec. 7.1, "Tested Algorithms"); Delta changes only speed, never the
-answer (Theorems 4.1/4.2 hold for any stepping schedule).  The library learns
+improving (Sec. 6.1, "Tested Algorithms"); Delta changes only speed, never the
+answer (Theorems 3.3/3.4 hold for any stepping schedule).  The library learns
 Delta instead with a small MLP; this module is the plain definition of that
 network, written out in float64:
 

@@ -1,9 +1,9 @@
 """Integer A* potential, written out from its definition.  TEST INFRASTRUCTURE ONLY.
 
-Paper Sec. 4.3: A* needs a heuristic h with h(u) <= w(u,v) + h(v) on every edge
-(consistency, which with h(t) = 0 implies admissibility; Fact 4.1 then makes
+Paper Sec. 3.3: A* needs a heuristic h with h(u) <= w(u,v) + h(v) on every edge
+(consistency, which with h(t) = 0 implies admissibility; Fact 3.1 then makes
 the reduced weights non-negative).  The paper uses Euclidean distance for k-NN
-graphs (Sec. 7 "Setup").  With integer weights w = round(1000 * length), the
+graphs (Sec. 6 "Setup").  With integer weights w = round(1000 * length), the
 literal floor(1000 * Euclid) is NOT always consistent (an edge of length 0.4004
 has w = 400 but the floors of 1000 * distance can differ by 401), so the
 library uses a scaled, fixed-point form whose consistency is certified edge by
@@ -72,7 +72,7 @@ def certificate_ok(off: np.ndarray, tgt: np.ndarray, w: np.ndarray, P: np.ndarra
 
 
 def consistent_for_anchor(off: np.ndarray, tgt: np.ndarray, w: np.ndarray, h: np.ndarray) -> bool:
-    """Fact 4.1 precondition: h(u) <= w(u,v) + h(v) on every CSR edge."""
+    """Fact 3.1 precondition: h(u) <= w(u,v) + h(v) on every CSR edge."""
     n = off.shape[0] - 1
     src = np.repeat(np.arange(n, dtype=np.int64), np.diff(off).astype(np.int64))
     return bool(np.all(h[src] <= w.astype(np.int64) + h[tgt.astype(np.int64)]))

@@ -4,8 +4,8 @@
  * library's query path never does.  It shares no code with the CUDA path.
  *
  * What it computes.  The paper's PPSP algorithms (Alg. 2 with the ET, A*, BiDS
- * and BiD-A* plug-ins of Table 2, and Multi-BiDS for batches, Sec. 5.2) return
- * exactly the shortest-path distance d(s,t) (Theorem 4.1 for BiDS, Theorem 4.2
+ * and BiD-A* plug-ins of Table 2, and Multi-BiDS for batches, Sec. 4.2) return
+ * exactly the shortest-path distance d(s,t) (Theorem 3.3 for BiDS, Theorem 3.4
  * for BiD-A*, on any stepping schedule).  The oracle is therefore the plain
  * definition of d(s,t): textbook binary-heap Dijkstra from s, stopped when t is
  * settled, with 64-bit unsigned sums.  Weights are non-negative integers

@@ -19,13 +19,13 @@
 //   BiDS        key = 2 d,                       prune 2 d >= mu   (mu/2 test doubled)
 //   BiD-A*      key = 2 d + rho_i(v) - rho_i(q_i), prune 2 d + rho_i(v) >= mu,
 //               rho_i(v) = h_{q_j}(v) - h_{q_i}(v)  (= 2 h_F for the forward search,
-//               2 h_B for the backward one: h_F = (h_t - h_s)/2 = -h_B, Sec. 4.5)
-//   Multi-BiDS  key = 2 d,                       prune 2 d >= mumax[i]  (Sec. 5.2)
+//               2 h_B for the backward one: h_F = (h_t - h_s)/2 = -h_B, Sec. 3.5)
+//   Multi-BiDS  key = 2 d,                       prune 2 d >= mumax[i]  (Sec. 4.2)
 //   ET          key = d,                         prune d >= mu, update when v = t
 //   A*          key = d + h_t(v) - h_t(s),       prune d + h_t(v) >= mu
 // The threshold step is 2 Delta on doubled keys and Delta otherwise.
 //
-// Correctness of mu.  Theorems 4.1/4.2 need, for the two ends x of some edge on
+// Correctness of mu.  Theorems 3.3/3.4 need, for the two ends x of some edge on
 // a shortest path, that mu is updated after both delta_i[x] and delta_j[x] hold
 // their final values.  The update at a successful WriteMin reads the other
 // search's value; when the two final writes race inside one step neither reader
@@ -90,7 +90,7 @@ __device__ __forceinline__ u64 isqrt_u64(u64 x) {
     return r;
 }
 
-// h_x(v) = floor(|P(v) - P(x)| / 2^F)  (integer potential, Sec. 4.3).
+// h_x(v) = floor(|P(v) - P(x)| / 2^F)  (integer potential, Sec. 3.3).
 __device__ __forceinline__ i64 pot_h(int2 px, int2 pv, u32 shift) {
     i64 dx = (i64)pv.x - (i64)px.x;
     i64 dy = (i64)pv.y - (i64)px.y;

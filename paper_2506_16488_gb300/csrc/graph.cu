@@ -54,7 +54,7 @@ static void parallel_for(u64 n, F f) {
     for (auto& t : th) t.join();
 }
 
-// The certified integer potential (Sec. 4.3, Fact 4.1): choose c and F, round
+// The certified integer potential (Sec. 3.3, Fact 3.1): choose c and F, round
 // P(v) = floor(p(v) * c * 2^F + 0.5), and check |P(u)-P(v)|^2 <= (2^F w)^2 on
 // every edge in exact integer arithmetic; shrink c until the check passes.
 static void build_potential(ppsp_graph* g, const u64* off, const u32* tgt, const u32* w, const float* xy) {

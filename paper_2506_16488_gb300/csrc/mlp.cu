@@ -2,7 +2,7 @@
 // fp32 accumulation, hand-written inference and training kernels.
 //
 // The paper chooses Delta of Delta*-stepping by doubling it until the running
-// time stops improving (Sec. 7.1); Delta only reorders work (Theorems 4.1/4.2
+// time stops improving (Sec. 6.1); Delta only reorders work (Theorems 3.3/3.4
 // hold for any stepping schedule), so a prediction can never change an answer.
 // The network predicts y = log2(Delta_best / Delta_default) from cheap per-group
 // features; Delta = Delta_default * 2^y, clamped.

@@ -1,4 +1,4 @@
-// Batch planning: query graph (Sec. 5.1), groups, team schedule, launches.
+// Batch planning: query graph (Sec. 4.1), groups, team schedule, launches.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -135,7 +135,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
             gqueries.push_back({u});
         }
     } else {
-        // Multi-BiDS: V_q = distinct endpoints, components of G_q (Sec. 5.2)
+        // Multi-BiDS: V_q = distinct endpoints, components of G_q (Sec. 4.2)
         std::unordered_map<u32, u32> vid;
         std::vector<u32> verts;
         auto get = [&](u32 v) {
@@ -247,9 +247,9 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
             s.pot_b = V[i];
             s.key_off = 0;
             if (o.mode == PPSP_BIDASTAR && G.scnt == 2) {
-                // Sec. 4.5 for an isolated pair: rho_i = h_partner - h_self, so the
+                // Sec. 3.5 for an isolated pair: rho_i = h_partner - h_self, so the
                 // two searches use exactly opposite potentials (h_F = -h_B, which
-                // Theorem 4.2 relies on).  Searches of larger query-graph components
+                // Theorem 3.4 relies on).  Searches of larger query-graph components
                 // run without a potential: a shared search cannot hold the opposite
                 // of every partner's potential at once.
                 s.pot = 1;

@@ -2,7 +2,7 @@
 //
 // Execution model.  A batch is a set of *groups*; a group is a set of k
 // single-source *searches* that share answers through *query edges* (a query
-// graph component, paper Sec. 5.1; a BiDS query is a group of two searches and
+// graph component, paper Sec. 4.1; a BiDS query is a group of two searches and
 // one query edge, Table 2).  One persistent cooperative kernel runs all groups.
 // Its CTAs are partitioned into *teams*; a team takes groups from its queue and
 // runs each to completion with the stepping loop of Alg. 2, synchronising its

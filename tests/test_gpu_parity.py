@@ -1,6 +1,6 @@
 """Parity of the CUDA path with the CPU oracle (bit-exact: all arithmetic is integer).
 
-Theorems 4.1 and 4.2 say BiDS and BiD-A* return d(s,t) for any stepping
+Theorems 3.3 and 3.4 say BiDS and BiD-A* return d(s,t) for any stepping
 schedule, so every launch configuration (Delta, frontier representation, block
 size, team size, layout, batch strategy) must give the oracle's answer exactly.
 """
@@ -236,7 +236,7 @@ def test_plan_writes_device_output(cfg1):
         plan.run(out.data_ptr())
         cnt = plan.sync()
         assert np.array_equal(out.cpu().numpy().view(np.uint64), want)
-        # Multi-BiDS: one search per distinct endpoint of the query graph (Sec. 5.2)
+        # Multi-BiDS: one search per distinct endpoint of the query graph (Sec. 4.2)
         uniq = {(min(a, b), max(a, b)) for a, b in pairs.tolist() if a != b}
         assert cnt["searches"] == len({v for e in uniq for v in e})
     plan.close()

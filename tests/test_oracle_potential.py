@@ -1,6 +1,6 @@
 """Pins for the oracle's integer A* potential (runs without a GPU).
 
-Definition (paper Sec. 4.3, Fact 4.1; the certified fixed-point form is spelled
+Definition (paper Sec. 3.3, Fact 3.1; the certified fixed-point form is spelled
 out in oracle/potential.py): h_x(v) = isqrt(floor(|P(v) - P(x)|^2 / 256)).
 """
 

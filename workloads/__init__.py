@@ -5,7 +5,7 @@ method's arithmetic (no relaxation, no pruning, no potential): both the CUDA
 path and the CPU oracle consume what it produces, and neither side imports the
 other.
 
-The graph shapes stand in for the paper's workloads (Sec. 7, "Setup" and the
+The graph shapes stand in for the paper's workloads (Sec. 6, "Setup" and the
 graph table): road networks and k-NN graphs are large-diameter, low-degree,
 planar-ish graphs with coordinates (jittered grids with deletions and short
 shortcuts here); social networks are power-law graphs (RMAT here), with

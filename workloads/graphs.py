@@ -5,7 +5,7 @@ by target id and hold both directions of each undirected edge with the same
 weight.  Vertex ids of grid graphs are row-major (``y * side + x``) after the
 largest-component relabelling, which keeps grid neighbours close in memory.
 
-Shapes (paper Sec. 7 "Setup" and its graph table): road graphs have average
+Shapes (paper Sec. 6 "Setup" and its graph table): road graphs have average
 degree about 2.5-2.7 and diameters in the thousands of hops; social graphs are
 power-law with integer weights uniform in a range.  The paper's real datasets
 are not available here, so these recipes stand in for their shapes only.

@@ -1,8 +1,8 @@
 """Seeded query sets: random pairs, near/mid/far terciles, stars and cliques.
 
-The paper picks query endpoints from the largest connected component (Sec. 7
+The paper picks query endpoints from the largest connected component (Sec. 6
 "Setup") and studies queries by distance percentile and by query-graph shape
-(Sec. 7.2: stars, cliques, random pairs).  Pairs are returned as uint32
+(Sec. 6.3: stars, cliques, random pairs).  Pairs are returned as uint32
 arrays of shape [k, 2] (source, target).
 """
 
