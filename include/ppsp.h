@@ -291,6 +291,33 @@ ppsp_status ppsp_delta_model_train(ppsp_delta_model* m, const float* feats, cons
                                    uint32_t epochs, float lr, float* loss_out);
 ppsp_status ppsp_graph_set_delta_model(ppsp_graph* g, int32_t mode, ppsp_delta_model* m);
 
+/*
+ * Allocation-free single query.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory (code running
+ * inside a memory pool it does not own, a serving process under a strict
+ * no-allocation policy, or a moment where cudaMalloc's implicit device
+ * synchronisation is not acceptable).  It answers one BiDS query (Sec. 3.4)
+ * without calling cudaMalloc, cudaFree or any allocating routine: all scratch
+ * lives in one fixed device array inside the library (about 13 MB, kept by
+ * every GPU that loads the library until the process exits).
+ *   d_offsets   device uint32[n+1], CSR offsets (4-byte aligned)
+ *   d_edges     device uint32[2m], (target, weight) per adjacency entry,
+ *               8-byte aligned; the CSR must be symmetric (undirected)
+ *   n, m        1 <= n <= PPSP_NOALLOC_MAX_N, m < 2^32
+ *   s, t        query endpoints (< n)
+ *   delta       stepping increment, 0 = mean edge weight (computed on the device)
+ *   d_dist_out  device uint64[1]: d(s, t) or PPSP_INF, written on `stream`
+ *   stream      cudaStream_t or NULL
+ * The call waits for its stream before returning the status.  All calls share
+ * the one array: calls that overlap on the GPU race and must not be issued.
+ * The first call on a device resolves the array's address and initialises it;
+ * make that call before any stream capture.  Errors: INVALID_ARG (null
+ * pointers, n above the limit, ids >= n), CUDA, TIMEOUT, OVERFLOW.
+ */
+#define PPSP_NOALLOC_MAX_N (1u << 20)
+ppsp_status ppsp_query_noalloc(const uint32_t* d_offsets, const uint32_t* d_edges, uint32_t n, uint64_t m,
+                               uint32_t s, uint32_t t, uint64_t delta, uint64_t* d_dist_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
