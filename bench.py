@@ -152,7 +152,8 @@ def cpu_baseline(g, pairs, labels, budget_s: float = 20.0):
     # a bounded, stratified sample: equal numbers of near, mid and far queries
     rng = np.random.default_rng(7)
     per = max(1, min(20, threads * 2))
-    idx = np.concatenate([rng.choice(np.nonzero(labels == b)[0], size=per, replace=False) for b in range(3)])
+    idx = np.concatenate([rng.choice(np.nonzero(labels == b)[0], size=min(per, int((labels == b).sum())),
+                                     replace=False) for b in np.unique(labels)])
     sample = pairs[idx]
     t0 = time.perf_counter()
     oracle.pairs_threaded(g.offsets, g.targets, g.weights, sample, threads)
@@ -223,12 +224,19 @@ def run_ours(args):
 
     wl, pairs, mode = load_workload(args.config)
     g = wl["graph"]
+    labels = wl.get("labels", np.zeros(pairs.shape[0], dtype=np.int32))
+    if args.queries and args.queries < pairs.shape[0]:
+        # an evenly strided subset keeps the near/mid/far mix
+        sel = np.linspace(0, pairs.shape[0] - 1, args.queries).astype(np.int64)
+        pairs, labels = pairs[sel], labels[sel]
     k = pairs.shape[0]
     workload = "road-like 1024x1024 grid (%d vertices, %d CSR entries), %d near/mid/far queries, %s" % (
         g.n, g.m, k, mode)
+    if args.max_ctas:
+        workload += f", at most {args.max_ctas} CTAs"
     G = ppsp.Graph.from_csr(g)
     stream = torch.cuda.Stream()
-    opts = dict(mode=mode, strategy="multi", stream=stream.cuda_stream)
+    opts = dict(mode=mode, strategy="multi", stream=stream.cuda_stream, max_ctas=args.max_ctas)
     delta_rule = "default (mean edge weight)"
     model = None
     if args.delta:
@@ -321,7 +329,7 @@ def run_ours(args):
     qps = world * k * args.steps / (total_ms / 1000.0)
     peak, peak_kind = read_peaks()
     achieved = alg_bytes / (ms_per_step / 1000.0) / 1e9
-    cpu = cpu_baseline(g, pairs, wl.get("labels", np.zeros(k, dtype=np.int32))) if world == 1 else None
+    cpu = cpu_baseline(g, pairs, labels) if world == 1 else None
     line = {
         "metric": "PPSP queries/sec (exact distances), batched vs plain one-at-a-time",
         "value": qps,
@@ -372,6 +380,8 @@ def main():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--delta", type=int, default=0)
     ap.add_argument("--no-learned", action="store_true", help="use the default Delta, not the learned model")
+    ap.add_argument("--queries", type=int, default=0, help="strided subset of the batch (profiling)")
+    ap.add_argument("--max-ctas", type=int, default=0, help="cap on resident CTAs (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -99,7 +99,9 @@ typedef struct {
                                 0 = default (about a few seconds)                          */
     void* stream;            /* cudaStream_t to run on; NULL = the legacy default stream    */
     uint32_t debug_flags;    /* test hooks, 0 in normal use (PPSP_DEBUG_*)                  */
-    uint32_t reserved[7];
+    uint32_t cuda_graph;     /* plans: 1 = capture the launches of ppsp_plan_run into a CUDA
+                                graph on a non-NULL stream and replay it (default 0)         */
+    uint32_t reserved[6];
 } ppsp_options;
 
 /* Test hook: device barriers wait for one arrival that never comes, so every
@@ -211,8 +213,11 @@ ppsp_status ppsp_batch(ppsp_graph* g, const uint32_t* pairs, uint64_t k, const p
  * graph, groups, schedule, device descriptors, search memory), ppsp_plan_run
  * launches the searches on opt->stream and writes d_dists_out (device
  * uint64[k], input order) before the stream's next work; ppsp_plan_sync waits
- * for the stream and returns the run's device status and counters.  A plan
- * keeps device memory until ppsp_plan_destroy and belongs to its graph.
+ * for the stream and returns the run's device status and counters.  With
+ * opt->cuda_graph = 1 and a non-NULL stream, the first run for a given
+ * d_dists_out captures the run's launches into a CUDA graph and every run
+ * replays it (if the driver refuses the capture, runs launch directly).  A
+ * plan keeps device memory until ppsp_plan_destroy and belongs to its graph.
  * Paths are not available through plans (use ppsp_batch).
  */
 ppsp_status ppsp_plan_create(ppsp_graph* g, const uint32_t* pairs, uint64_t k,
@@ -255,6 +260,9 @@ ppsp_status ppsp_plan_features(const ppsp_plan* p, float* out, uint64_t cap, uin
  * run), BUFFER_TOO_SMALL, CUDA.
  */
 ppsp_status ppsp_plan_group_times(ppsp_plan* p, uint64_t* out_ns, uint64_t cap, uint64_t* ngroups);
+
+/* 1 if the plan's last run replayed a captured CUDA graph, else 0. */
+ppsp_status ppsp_plan_uses_graph(const ppsp_plan* p, int32_t* out);
 
 /*
  * Learned stepping increment.  The paper tunes Delta of Delta*-stepping by

@@ -82,9 +82,11 @@ __device__ __forceinline__ u64 global_ns() {
     return t;
 }
 
-// Exact floor(sqrt(x)) for x < 2^62: float64 estimate, then integer correction.
+// Exact floor(sqrt(x)) for x < 2^62: a floating-point estimate, then integer
+// correction.  Below 2^48 the float32 estimate is within 1 of the result
+// (relative error about 2^-24 on a value below 2^24); above, float64.
 __device__ __forceinline__ u64 isqrt_u64(u64 x) {
-    u64 r = (u64)sqrt((double)x);
+    u64 r = (x < (1ull << 48)) ? (u64)sqrtf((float)x) : (u64)sqrt((double)x);
     while (r * r > x) --r;
     while ((r + 1) * (r + 1) <= x) ++r;
     return r;
@@ -531,6 +533,110 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
 }
 
 // ----------------------------------------------------------------------------
+// paths: meeting vertex, then a warp walks tight edges back to each source
+// ----------------------------------------------------------------------------
+// Walk from x0 towards the source of search i along edges (u, x) with
+// delta_i[u] + w(u, x) = delta_i[x] (smallest u first), writing x0, ..., q_i to
+// out[start ..] while below cap.  Weights are >= 1, so delta_i strictly
+// decreases along the walk; every such u has an exact delta_i because x does.
+template <typename D, int B>
+__device__ u64 walk_back(const EngineArgs& a, GCtx<D>& c, const Smem<B>& sm, u32 x0, u32 i, u32* out,
+                         u64 cap, u64 start) {
+    const u32 lane = threadIdx.x & 31;
+    u32 x = x0;
+    u64 idx = start;
+    if (lane == 0 && idx < cap) out[idx] = x;
+    ++idx;
+    for (u32 steps = 0; x != sm.src[i]; ++steps) {
+        if (steps > c.n) {  // cannot happen with positive weights; never loop forever
+            if (lane == 0) atomicOr(a.err, ERRB_INTERNAL);
+            break;
+        }
+        const u64 dx = ld_dist(c.dist + flat_of(c.G, c.n, x, i));
+        const u32 b0 = __ldg(a.g.off + x), b1 = __ldg(a.g.off + x + 1);
+        u32 best = NONE;
+        for (u32 e = b0 + lane; e < b1; e += 32) {
+            const uint2 ew = __ldg(a.g.edges + e);
+            const u64 du = ld_dist(c.dist + flat_of(c.G, c.n, ew.x, i));
+            if (du != DT<D>::INF && du + ew.y == dx && ew.x < best) best = ew.x;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (best == NONE) {
+            if (lane == 0) atomicOr(a.err, ERRB_INTERNAL);
+            break;
+        }
+        x = best;
+        if (lane == 0 && idx < cap) out[idx] = x;
+        ++idx;
+    }
+    return idx - start;
+}
+
+template <typename D, int B>
+__device__ bool find_paths(const EngineArgs& a, const TeamCtx& tc, GCtx<D>& c, Smem<B>& sm, u32 flat_range) {
+    const GroupDev& G = c.G;
+    const u32 t = threadIdx.x;
+    if (G.mode == GM_BIDIR) {
+        // meeting vertex of each query edge: smallest v with delta_a[v] + delta_b[v] = mu
+        const u32 tn = ld_volatile(&c.slot.st->touched_n);
+        const bool tov = ld_volatile(&c.slot.st->touched_overflow) != 0;
+        const u32 lim = tov ? flat_range : min(tn, c.slot.tcap);
+        for (u32 k = tc.rank * B + t; k < lim; k += tc.size * B) {
+            const u32 f = tov ? k : __ldcg(c.slot.touched + k);
+            u32 v, i;
+            decode_flat(G, c.n, f, v, i);
+            if (i >= G.scnt) continue;
+            const u64 di = ld_dist(c.dist + f);
+            if (di == DT<D>::INF) continue;
+            for (u32 p = 0; p < sm.pcnt[i]; ++p) {
+                const PartnerDev pd = partner(a, sm, i, p);
+                if (pd.j < i) continue;  // each query edge from its lower-index end
+                const u64 dj = ld_dist(c.dist + flat_of(G, c.n, v, pd.j));
+                if (dj != DT<D>::INF && di + dj == ldcg64(a.mu + pd.qe)) atomicMin(a.meet + pd.qe, v);
+            }
+        }
+    } else if (tc.rank == 0 && t == 0) {
+        a.meet[G.qbeg] = G.target;
+    }
+    if (!team_sync(tc, a, &sm.flag)) return false;
+    const u32 warps = B / 32, lane = t & 31, wid = t >> 5;
+    for (u32 q = tc.rank * warps + wid; q < G.qcnt; q += tc.size * warps) {
+        const u32 qe = G.qbeg + q;
+        const u64 mu = ldcg64(a.mu + qe);
+        u64 len = 0;
+        if (mu != INF64) {
+            const QEdgeDev e = a.qedges[qe];
+            const u32 m = ld_volatile(a.meet + qe);
+            const u64 cap = a.path_off[qe + 1] - a.path_off[qe];
+            u32* out = a.path_buf + a.path_off[qe];
+            if (m == NONE) {
+                if (lane == 0) atomicOr(a.err, ERRB_INTERNAL);
+            } else {
+                // q_a .. m: walk m -> q_a, then reverse in place
+                const u64 na = walk_back<D, B>(a, c, sm, m, e.a, out, cap, 0);
+                if (na <= cap) {
+                    for (u64 k = lane; k < na / 2; k += 32) {
+                        const u32 x = out[k];
+                        out[k] = out[na - 1 - k];
+                        out[na - 1 - k] = x;
+                    }
+                }
+                __syncwarp();
+                len = na;
+                if (G.mode == GM_BIDIR) {
+                    // m .. q_b along delta_b (m itself already written)
+                    const u64 nb = walk_back<D, B>(a, c, sm, m, e.b, out, cap, na - 1);
+                    len = na + nb - 1;
+                }
+            }
+        }
+        if (lane == 0) a.path_len[qe] = len;
+    }
+    return team_sync(tc, a, &sm.flag);
+}
+
+// ----------------------------------------------------------------------------
 // one group
 // ----------------------------------------------------------------------------
 template <typename D, int B>
@@ -752,6 +858,9 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
         if (!team_sync(tc, a, &sm.flag)) return false;
         dense_cur = c.dense_nxt;
     }
+
+    // ---- paths (optional), before the distances are reset ----
+    if (a.path_buf != nullptr && !find_paths<D, B>(a, tc, c, sm, flat_range)) return false;
 
     // ---- tidy the slot ----
     if (exit_count > 0) {

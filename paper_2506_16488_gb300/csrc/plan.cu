@@ -39,6 +39,16 @@ struct ppsp_plan {
     float* d_feats = nullptr;
     ppsp_delta_model* model = nullptr;
     u64 delta_default = 1;
+    // paths (ppsp_query / ppsp_batch with want_paths)
+    bool paths = false;
+    std::vector<u64> path_off;  // [qedges + 1]
+    void* d_paths = nullptr;    // path buffer, offsets, lengths, meeting vertices
+    u32* d_meet = nullptr;
+    // CUDA-graph replay of plan_run (per output pointer)
+    cudaGraphExec_t gexec = nullptr;
+    u64* gexec_out = nullptr;
+    bool graph_failed = false;
+    bool last_used_graph = false;
 };
 
 namespace {
@@ -81,9 +91,19 @@ ppsp_status check_options(const ppsp_graph* g, const ppsp_options& o) {
 
 }  // namespace
 
+static void plan_free_partial(ppsp_plan* P) {
+    for (Slot* x : P->slots) slot_release(P->g, x);
+    P->slots.clear();
+    cudaFree(P->d_arena);
+    cudaFree(P->d_paths);
+    P->d_arena = nullptr;
+    P->d_paths = nullptr;
+    cudaGetLastError();
+}
+
 // Build everything from host pairs.  Separated so ppsp_query can reuse it.
 static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64_t k, const ppsp_options* opt_in,
-                                    bool single_query, ppsp_plan** out) {
+                                    bool single_query, ppsp_plan** out, const u64* path_caps = nullptr) {
     ppsp_options o;
     if (opt_in)
         o = *opt_in;
@@ -92,6 +112,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     ppsp_status st = check_options(g, o);
     if (st != PPSP_OK) return st;
     if (k && !pairs) return PPSP_ERR_INVALID_ARG;
+    if (o.want_paths && (!path_caps || g->info.has_zero_weight)) return PPSP_ERR_UNSUPPORTED;
     const u64 n = g->n;
     for (u64 q = 0; q < 2 * k; ++q)
         if (pairs[q] >= n) return PPSP_ERR_INVALID_ARG;
@@ -487,6 +508,37 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     P->d_runstate = base + o_run;
     P->d_map = (u32*)(base + o_map);
     P->d_feats = (float*)(base + o_feat);
+    if (o.want_paths) {
+        const u64 NQ = P->qedges.size();
+        std::vector<u64> cap(NQ, 0);
+        for (u64 q = 0; q < k; ++q)
+            if (P->map[q] != NONE) cap[P->map[q]] = std::max(cap[P->map[q]], path_caps[q]);
+        P->path_off.assign(NQ + 1, 0);
+        for (u64 e = 0; e < NQ; ++e) P->path_off[e + 1] = P->path_off[e] + cap[e];
+        const size_t b_buf = ((P->path_off[NQ] * 4) + 255) & ~(size_t)255;
+        const size_t b_off = ((NQ + 1) * 8 + 255) & ~(size_t)255;
+        const size_t b_len = (NQ * 8 + 255) & ~(size_t)255;
+        const size_t b_meet = (NQ * 4 + 255) & ~(size_t)255;
+        ce = cudaMalloc(&P->d_paths, std::max<size_t>(256, b_buf + b_off + b_len + b_meet));
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            plan_free_partial(P.get());
+            return ce == cudaErrorMemoryAllocation ? PPSP_ERR_OOM : PPSP_ERR_CUDA;
+        }
+        char* pb = (char*)P->d_paths;
+        a.path_buf = (u32*)pb;
+        a.path_off = (const u64*)(pb + b_buf);
+        a.path_len = (u64*)(pb + b_buf + b_off);
+        P->d_meet = (u32*)(pb + b_buf + b_off + b_len);
+        a.meet = P->d_meet;
+        ce = cudaMemcpy((void*)a.path_off, P->path_off.data(), (NQ + 1) * 8, cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            plan_free_partial(P.get());
+            return PPSP_ERR_CUDA;
+        }
+        P->paths = true;
+    }
     *out = P.release();
     return PPSP_OK;
 }
@@ -498,15 +550,62 @@ static void plan_free(ppsp_plan* P) {
     else
         cudaDeviceSynchronize();
     for (Slot* s : P->slots) slot_release(P->g, s);
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
     cudaFree(P->d_arena);
+    cudaFree(P->d_paths);
     cudaGetLastError();
     delete P;
 }
 
+static ppsp_status plan_launch_direct(ppsp_plan* P, u64* d_out);
+
+// Capture the launches of one run into a CUDA graph (once per output pointer)
+// and replay it; any capture failure falls back to direct launches.
 static ppsp_status plan_launch(ppsp_plan* P, u64* d_out) {
+    P->last_used_graph = false;
+    if (!P->opt.cuda_graph || P->stream == nullptr || P->graph_failed || P->g->pool_dirty)
+        return plan_launch_direct(P, d_out);
+    if (P->gexec == nullptr || P->gexec_out != d_out) {
+        if (P->gexec) {
+            cudaGraphExecDestroy(P->gexec);
+            P->gexec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            P->graph_failed = true;
+            return plan_launch_direct(P, d_out);
+        }
+        ppsp_status st = plan_launch_direct(P, d_out);
+        cudaError_t ce = cudaStreamEndCapture(P->stream, &graph);
+        if (st != PPSP_OK || ce != cudaSuccess || graph == nullptr) {
+            cudaGetLastError();
+            if (graph) cudaGraphDestroy(graph);
+            P->graph_failed = true;
+            return plan_launch_direct(P, d_out);
+        }
+        ce = cudaGraphInstantiate(&P->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            P->gexec = nullptr;
+            P->graph_failed = true;
+            return plan_launch_direct(P, d_out);
+        }
+        P->gexec_out = d_out;
+    }
+    PPSP_CUDA_TRY(cudaGraphLaunch(P->gexec, P->stream));
+    P->launched = true;
+    P->last_used_graph = true;
+    return PPSP_OK;
+}
+
+static ppsp_status plan_launch_direct(ppsp_plan* P, u64* d_out) {
     ppsp_status st = pool_scrub(P->g, P->stream);
     if (st != PPSP_OK) return st;
     PPSP_CUDA_TRY(cudaMemsetAsync(P->d_runstate, 0, P->runstate_bytes, P->stream));
+    if (P->paths && !P->qedges.empty())
+        PPSP_CUDA_TRY(cudaMemsetAsync(P->d_meet, 0xFF, P->qedges.size() * 4, P->stream));
     if (P->model && !P->groups.empty()) {
         // learned Delta per group, written into the device group descriptors
         st = mlp_launch_infer(P->model, P->d_feats, P->groups.size(), nullptr, const_cast<GroupDev*>(P->args.groups),
@@ -606,6 +705,12 @@ ppsp_status ppsp_plan_group_times(ppsp_plan* p, uint64_t* out_ns, uint64_t cap, 
     return PPSP_OK;
 }
 
+ppsp_status ppsp_plan_uses_graph(const ppsp_plan* p, int32_t* out) {
+    if (!p || !out) return PPSP_ERR_INVALID_ARG;
+    *out = p->last_used_graph ? 1 : 0;
+    return PPSP_OK;
+}
+
 void ppsp_plan_destroy(ppsp_plan* p) {
     if (!p) return;
     ppsp_graph* g = p->g;
@@ -613,10 +718,22 @@ void ppsp_plan_destroy(ppsp_plan* p) {
     plan_free(p);
 }
 
+struct HostPaths {
+    uint32_t* buf = nullptr;          // caller's path buffer
+    const uint64_t* offsets = nullptr;  // per query [k+1] (batch), or null (single query)
+    uint64_t single_cap = 0;          // single query: capacity
+    uint64_t* lens = nullptr;         // per query needed lengths
+};
+
 static ppsp_status run_host(ppsp_graph* g, const uint32_t* pairs, uint64_t k, const ppsp_options* opt,
-                            bool single, uint64_t* dists_out, ppsp_counters* counters) {
+                            bool single, uint64_t* dists_out, ppsp_counters* counters, const HostPaths* hp) {
     ppsp_plan* P = nullptr;
-    ppsp_status st = plan_create_impl(g, pairs, k, opt, single, &P);
+    std::vector<u64> caps;
+    if (hp) {
+        caps.resize(k);
+        for (u64 q = 0; q < k; ++q) caps[q] = hp->offsets ? hp->offsets[q + 1] - hp->offsets[q] : hp->single_cap;
+    }
+    ppsp_status st = plan_create_impl(g, pairs, k, opt, single, &P, hp ? caps.data() : nullptr);
     if (st != PPSP_OK) return st;
     u64* d_out = nullptr;
     cudaError_t ce = cudaMalloc(&d_out, std::max<u64>(1, k) * 8);
@@ -634,6 +751,45 @@ static ppsp_status run_host(ppsp_graph* g, const uint32_t* pairs, uint64_t k, co
             st = PPSP_ERR_CUDA;
         }
     }
+    if (st == PPSP_OK && hp && P->paths) {
+        // device paths are per query edge, oriented from its first to its
+        // second endpoint; copy (or reverse) them into each query's slice
+        const u64 NQ = P->qedges.size();
+        std::vector<u64> plen(NQ, 0);
+        std::vector<u32> pbuf(P->path_off[NQ]);
+        if (NQ) {
+            ce = cudaMemcpy(plen.data(), P->args.path_len, NQ * 8, cudaMemcpyDeviceToHost);
+            if (ce == cudaSuccess && !pbuf.empty())
+                ce = cudaMemcpy(pbuf.data(), P->args.path_buf, pbuf.size() * 4, cudaMemcpyDeviceToHost);
+            if (ce != cudaSuccess) {
+                cudaGetLastError();
+                st = PPSP_ERR_CUDA;
+            }
+        }
+        bool small = false;
+        for (u64 q = 0; q < k && st == PPSP_OK; ++q) {
+            const u32 s = pairs[2 * q], t = pairs[2 * q + 1];
+            uint32_t* dst = hp->buf + (hp->offsets ? hp->offsets[q] : 0);
+            const u64 cap = caps[q];
+            u64 len = 0;
+            if (s == t) {
+                len = 1;
+                if (cap >= 1 && hp->buf) dst[0] = s;
+            } else if (dists_out[q] != PPSP_INF) {
+                const u32 qe = P->map[q];
+                len = plen[qe];
+                if (len <= cap && len <= P->path_off[qe + 1] - P->path_off[qe] && hp->buf) {
+                    const u32* src = pbuf.data() + P->path_off[qe];
+                    const bool fwd = (P->qedge_ends[qe].first == s);
+                    for (u64 x = 0; x < len; ++x) dst[x] = fwd ? src[x] : src[len - 1 - x];
+                } else {
+                    small = true;
+                }
+            }
+            if (hp->lens) hp->lens[q] = len;
+        }
+        if (st == PPSP_OK && small) st = PPSP_ERR_BUFFER_TOO_SMALL;
+    }
     cudaFree(d_out);
     plan_free(P);
     return st;
@@ -642,25 +798,36 @@ static ppsp_status run_host(ppsp_graph* g, const uint32_t* pairs, uint64_t k, co
 ppsp_status ppsp_query(ppsp_graph* g, uint32_t s, uint32_t t, const ppsp_options* opt, uint64_t* dist_out,
                        uint32_t* path_buf, uint64_t path_cap, uint64_t* path_len) {
     if (!g || !dist_out) return PPSP_ERR_INVALID_ARG;
-    if (opt && opt->want_paths) return PPSP_ERR_UNSUPPORTED;
-    (void)path_buf;
-    (void)path_cap;
     if (path_len) *path_len = 0;
     uint32_t pr[2] = {s, t};
     std::lock_guard<std::mutex> lk(g->mu);
-    return run_host(g, pr, 1, opt, true, dist_out, nullptr);
+    if (opt && opt->want_paths) {
+        if (path_cap && !path_buf) return PPSP_ERR_INVALID_ARG;
+        HostPaths hp;
+        hp.buf = path_buf;
+        hp.single_cap = path_cap;
+        hp.lens = path_len;
+        return run_host(g, pr, 1, opt, true, dist_out, nullptr, &hp);
+    }
+    return run_host(g, pr, 1, opt, true, dist_out, nullptr, nullptr);
 }
 
 ppsp_status ppsp_batch(ppsp_graph* g, const uint32_t* pairs, uint64_t k, const ppsp_options* opt,
                        uint64_t* dists_out, uint32_t* paths_buf, const uint64_t* path_offsets, uint64_t* path_lens,
                        ppsp_counters* counters) {
     if (!g || (k && (!pairs || !dists_out))) return PPSP_ERR_INVALID_ARG;
-    if (opt && opt->want_paths) return PPSP_ERR_UNSUPPORTED;
-    (void)paths_buf;
-    (void)path_offsets;
-    (void)path_lens;
     std::lock_guard<std::mutex> lk(g->mu);
-    return run_host(g, pairs, k, opt, false, dists_out, counters);
+    if (opt && opt->want_paths) {
+        if (k && (!path_offsets || !paths_buf)) return PPSP_ERR_INVALID_ARG;
+        for (u64 q = 0; q < k; ++q)
+            if (path_offsets[q + 1] < path_offsets[q]) return PPSP_ERR_INVALID_ARG;
+        HostPaths hp;
+        hp.buf = paths_buf;
+        hp.offsets = path_offsets;
+        hp.lens = path_lens;
+        return run_host(g, pairs, k, opt, false, dists_out, counters, &hp);
+    }
+    return run_host(g, pairs, k, opt, false, dists_out, counters, nullptr);
 }
 
 }  // extern "C"

@@ -139,6 +139,11 @@ struct EngineArgs {
     u32* err;
     EngineCounters* counters;
     u64* group_ns;        // [groups] device time of each group, or null
+    // optional paths (null path_buf = distances only)
+    u32* meet;            // [num_qedges] meeting vertex, NONE-initialised per run
+    u32* path_buf;        // concatenated per-query-edge path buffers
+    const u64* path_off;  // [num_qedges + 1] buffer offsets (capacity = difference)
+    u64* path_len;        // [num_qedges] vertices on the path (needed length)
 };
 
 // ---- host helpers shared between translation units ----

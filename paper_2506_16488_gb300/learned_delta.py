@@ -170,6 +170,28 @@ def build_and_train(mode: str, out_dir: str = WEIGHTS_DIR, epochs: int = 600, lo
     return meta
 
 
+def evaluate(mode: str, log=print) -> dict:
+    """Regret of the saved model on the held-out road-like benchmark queries
+    (the 1,000 near/mid/far pairs; training used other seeds)."""
+    from workloads import config_workload
+
+    wl = config_workload(2)
+    g, pairs = wl["graph"], wl["batches"]["nmf"]
+    model = load_model(mode)
+    if model is None:
+        raise FileNotFoundError(weights_path(mode))
+    with ppsp.Graph.from_csr(g) as G:
+        feats, times, default = sweep(G, pairs, mode)
+    y = model.predict(feats)
+    res = {"mode": mode, "eval_set": "road1024 near/mid/far (bench queries)", "groups": int(feats.shape[0]),
+           "regret_learned": regret(times, y), "regret_default": default_regret(times),
+           "best_grid_hist": {str(j): int((labels_from_times(times) == j).sum()) for j in GRID},
+           "pred_mean": float(y.mean())}
+    model.close()
+    log(json.dumps(res))
+    return res
+
+
 if __name__ == "__main__":
     import sys
 
@@ -178,6 +200,10 @@ if __name__ == "__main__":
     import __graft_entry__
 
     __graft_entry__.build()
-    modes = sys.argv[1:] or ["bidastar", "bids"]
-    for md in modes:
-        build_and_train(md)
+    args = sys.argv[1:]
+    if args and args[0] == "eval":
+        for md in args[1:] or ["bidastar", "bids"]:
+            evaluate(md)
+    else:
+        for md in args or ["bidastar", "bids"]:
+            build_and_train(md)

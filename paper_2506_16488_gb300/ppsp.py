@@ -52,7 +52,8 @@ class Options(ctypes.Structure):
         ("spin_limit", ctypes.c_uint64),
         ("stream", ctypes.c_void_p),
         ("debug_flags", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 7),
+        ("cuda_graph", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 6),
     ]
 
 
@@ -128,6 +129,7 @@ def load(build_if_missing: bool = False):
             "ppsp_potential_eval": (S, [p, u32, p, u64, p]),
             "ppsp_plan_features": (S, [p, p, u64, p]),
             "ppsp_plan_group_times": (S, [p, p, u64, p]),
+            "ppsp_plan_uses_graph": (S, [p, p]),
             "ppsp_delta_model_create": (S, [p, p]),
             "ppsp_delta_model_destroy": (None, [p]),
             "ppsp_delta_model_get_params": (S, [p, p]),
@@ -160,7 +162,8 @@ def _ptr(a: Optional[np.ndarray]):
 def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, frontier="auto",
                  layout="auto", strategy="multi", block_threads: int = 0, team_ctas: int = 0,
                  big_team_ctas: int = 0, dense_den: int = 0, want_paths: bool = False, max_ctas: int = 0,
-                 spin_limit: int = 0, stream: int | None = None, debug_flags: int = 0) -> Options:
+                 spin_limit: int = 0, stream: int | None = None, debug_flags: int = 0,
+                 cuda_graph: bool = False) -> Options:
     o = Options()
     load().ppsp_options_init(ctypes.byref(o))
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
@@ -178,6 +181,7 @@ def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, 
     o.spin_limit = spin_limit
     o.stream = stream
     o.debug_flags = debug_flags
+    o.cuda_graph = int(bool(cuda_graph))
     return o
 
 
@@ -251,6 +255,34 @@ class Graph:
         _check(st, "ppsp_batch")
         return (out, c.as_dict()) if return_counters else out
 
+    def query_path(self, s: int, t: int, cap: int = 1 << 16, **opts) -> tuple:
+        """(status, distance, path as uint32 array or None if it did not fit, needed length)."""
+        o = make_options(want_paths=True, **opts)
+        d = ctypes.c_uint64(0)
+        plen = ctypes.c_uint64(0)
+        buf = np.zeros(max(1, cap), dtype=np.uint32)
+        st = load().ppsp_query(self._h, s, t, ctypes.byref(o), ctypes.byref(d), _ptr(buf), cap, ctypes.byref(plen))
+        n = int(plen.value)
+        path = buf[:n].copy() if st == OK else None
+        return int(st), int(d.value), path, n
+
+    def batch_paths(self, pairs, caps, **opts) -> tuple:
+        """(status, distances, list of paths (None where it did not fit), needed lengths)."""
+        o = make_options(want_paths=True, **opts)
+        pa = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+        k = pa.shape[0]
+        caps = np.broadcast_to(np.asarray(caps, dtype=np.uint64), (k,))
+        off = np.zeros(k + 1, dtype=np.uint64)
+        np.cumsum(caps, out=off[1:])
+        buf = np.zeros(max(1, int(off[-1])), dtype=np.uint32)
+        out = np.zeros(k, dtype=np.uint64)
+        lens = np.zeros(k, dtype=np.uint64)
+        st = load().ppsp_batch(self._h, _ptr(pa), k, ctypes.byref(o), _ptr(out), _ptr(buf), _ptr(off), _ptr(lens),
+                               None)
+        paths = [buf[int(off[q]):int(off[q]) + int(lens[q])].copy() if lens[q] <= caps[q] else None
+                 for q in range(k)]
+        return int(st), out, paths, lens
+
     def batch_status(self, pairs, **opts) -> tuple:
         o = make_options(**opts)
         pa = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
@@ -312,6 +344,11 @@ class Plan:
         out = np.zeros((ng.value, MLP_FEATURES), dtype=np.float32)
         _check(load().ppsp_plan_features(self._h, _ptr(out), ng.value, ctypes.byref(ng)), "ppsp_plan_features")
         return out
+
+    def uses_graph(self) -> bool:
+        v = ctypes.c_int32(0)
+        _check(load().ppsp_plan_uses_graph(self._h, ctypes.byref(v)), "ppsp_plan_uses_graph")
+        return bool(v.value)
 
     def group_times(self) -> np.ndarray:
         """Device ns per group of the last run, uint64 [groups]."""

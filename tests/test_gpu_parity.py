@@ -271,3 +271,20 @@ def test_cfg4_small_mixed_clique():
     with ppsp.Graph.from_csr(g) as G:
         for mode in ("bidastar", "bids"):
             assert np.array_equal(G.batch(pairs, mode=mode), want)
+
+
+def test_plan_replays_a_cuda_graph(cfg1):
+    torch = pytest.importorskip("torch")
+    g, pairs, want, G = cfg1
+    stream = torch.cuda.Stream()
+    out = torch.zeros(pairs.shape[0], dtype=torch.int64, device="cuda")
+    out2 = torch.zeros(pairs.shape[0], dtype=torch.int64, device="cuda")
+    plan = G.plan(pairs, mode="bidastar", stream=stream.cuda_stream, cuda_graph=True)
+    for dst in (out, out, out2, out):
+        dst.zero_()
+        torch.cuda.synchronize()
+        plan.run(dst.data_ptr())
+        plan.sync()
+        assert np.array_equal(dst.cpu().numpy().view(np.uint64), want)
+        assert plan.uses_graph()
+    plan.close()
