@@ -98,12 +98,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+WORKLOAD_NAMES = {
+    1: "64x64 jittered grid, 100 random pairs",
+    2: "road-like 1024x1024 grid, 1000 near/mid/far queries",
+    3: "RMAT scale 22 (edge factor 16), 64 random pairs + 64-leaf star + 11-clique",
+    4: "road-like 2048x2048 grid, 1552 random pairs + 32-clique (496 pairs)",
+    5: "road-like 4096x4096 grid, uint64 distances, Poisson arrivals (serving)",
+}
+
+
 def load_workload(cfg: int):
     from workloads import config_workload
 
     wl = config_workload(cfg)
-    pairs = next(iter(wl["batches"].values()))
-    mode = {"bids": "bids", "bidastar": "bidastar", "multi_astar": "bidastar", "serving": "bids"}[wl["mode"]]
+    # every batch of the configuration, as one batch (its query graph keeps
+    # the random pairs, the star and the clique as separate components)
+    pairs = np.concatenate(list(wl["batches"].values()))
+    mode = {"bids": "bids", "bidastar": "bidastar", "multi_astar": "bidastar", "serving": "bidastar"}[wl["mode"]]
     return wl, pairs, mode
 
 
@@ -230,8 +241,8 @@ def run_ours(args):
         sel = np.linspace(0, pairs.shape[0] - 1, args.queries).astype(np.int64)
         pairs, labels = pairs[sel], labels[sel]
     k = pairs.shape[0]
-    workload = "road-like 1024x1024 grid (%d vertices, %d CSR entries), %d near/mid/far queries, %s" % (
-        g.n, g.m, k, mode)
+    workload = "%s (%d vertices, %d CSR entries, %d queries per step), %s" % (
+        WORKLOAD_NAMES[args.config], g.n, g.m, k, mode)
     if args.max_ctas:
         workload += f", at most {args.max_ctas} CTAs"
     G = ppsp.Graph.from_csr(g)
@@ -371,6 +382,63 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serving(args):
+    """Config 5: continuous-batching serving on the 4096^2 road-like graph with
+    uint64 distances; Poisson arrivals of singles and batches of up to 256
+    pairs at several offered rates; p50/p99 latency and sustained queries/s."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2506_16488_gb300 import learned_delta, ppsp
+    from paper_2506_16488_gb300.serving import GpuExecutor, Scheduler, memory_model, poisson_arrivals, serve
+    from workloads import config_workload
+
+    wl = config_workload(5, small=args.small)
+    g = wl["graph"]
+    G = ppsp.Graph.from_csr(g)
+    mode = "bidastar"
+    model = None if args.no_learned else learned_delta.load_model(mode)
+    if model is not None:
+        G.set_delta_model(mode, model)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.6 * free)
+    lanes = 4
+    lane_ctas = max(1, (2 * torch.cuda.get_device_properties(0).multi_processor_count) // lanes)
+    rng = np.random.default_rng(5003)
+    src = lambda k: g.lcc[rng.integers(0, g.lcc.shape[0], size=(k, 2))]
+    ex = GpuExecutor(G, lanes, mode=mode, dist_bits=64, lane_ctas=lane_ctas)
+    # warm-up: slot pool and code paths
+    serve(poisson_arrivals(2000, 0.2, src, seed=5004), ex, Scheduler(lanes, 256, budget, memory_model(g.n, lane_ctas, 64)))
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
+    sampler.start()
+    rates = []
+    for rate in args.rates:
+        arr = poisson_arrivals(rate, args.duration, src, seed=int(rate))
+        out = serve(arr, ex, Scheduler(lanes, 256, budget, memory_model(g.n, lane_ctas, 64)))
+        bad = [r for r in out["requests"] if r.status != 0]
+        rates.append({"offered_qps": rate, "sustained_qps": out["qps"], "p50_ms": out["latency_p50_ms"],
+                      "p99_ms": out["latency_p99_ms"], "queries": out["queries"], "requests": len(arr),
+                      "rejected": out["rejected"], "failed": len(bad)})
+    clocks = sampler.stop()
+    best = max(rates, key=lambda r: r["sustained_qps"] or 0)
+    line = {
+        "metric": "PPSP queries/sec (exact distances) served with continuous batching",
+        "value": best["sustained_qps"], "unit": "queries/s", "n_gpus": 1, "steps": len(rates), "warmup": 1,
+        "ms_per_step": 1000.0 * args.duration, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD_NAMES[5]} ({g.n} vertices, {g.m} CSR entries)", "lanes": lanes,
+                   "lane_ctas": lane_ctas, "memory_budget_bytes": budget,
+                   "delta": "learned MLP" if model is not None else "default (mean edge weight)"},
+        "rates": rates, "clocks": clocks,
+        "e2e": {"value": best["sustained_qps"], "unit": "queries/s", "h2d_bytes_per_step": None,
+                "d2h_bytes_per_step": None},
+    }
+    print(json.dumps(line), flush=True)
+    G.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,7 +450,14 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="use the default Delta, not the learned model")
     ap.add_argument("--queries", type=int, default=0, help="strided subset of the batch (profiling)")
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on resident CTAs (profiling)")
+    ap.add_argument("--rates", type=float, nargs="*", default=[1000, 5000, 20000, 50000],
+                    help="serving (config 5): offered query rates")
+    ap.add_argument("--duration", type=float, default=2.0, help="serving (config 5): seconds per rate")
+    ap.add_argument("--small", action="store_true", help="serving (config 5): small graph (tests)")
     args = ap.parse_args()
+    if args.impl != "reference" and args.config == 5:
+        run_serving(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

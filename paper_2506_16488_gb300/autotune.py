@@ -1,0 +1,122 @@
+"""Autotuner for the launch configuration of a batch.
+
+The knobs change only speed, never answers (Theorems 3.3/3.4 hold for any
+schedule): threads per CTA, CTAs per pair team, CTAs per multi-search team,
+the sparse/dense frontier threshold (App. B), the distance layout of
+multi-search groups, and the frontier policy.  The tuner runs the batch's plan
+with one knob changed at a time (coordinate descent from the library's
+defaults), keeps the fastest setting (minimum of a few device-timed runs),
+checks that every run returns the same distances, and caches the result per
+(graph, batch shape, mode) in a JSON file.
+"""
+
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+import numpy as np
+
+from . import ppsp
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.path.join(HERE, "tuning", "cache.json")
+
+SPACE = (
+    ("block_threads", (512, 256, 1024)),
+    ("team_ctas", (0, 1, 2, 4, 8)),
+    ("big_team_ctas", (0, 8, 16, 32, 64, 128)),
+    ("dense_den", (16, 4, 64, 1024)),
+    ("layout", ("interleaved", "stacked")),
+    ("frontier", ("auto", "sparse")),
+)
+
+
+def signature(G: ppsp.Graph, pairs: np.ndarray, mode: str, dist_bits: int = 32) -> str:
+    info = G.info()
+    p = np.asarray(pairs).reshape(-1, 2)
+    ends, counts = np.unique(p[p[:, 0] != p[:, 1]].ravel(), return_counts=True)
+    shape = {"n": int(info["n"]), "m": int(info["m"]), "w": round(float(info["w_mean"])),
+             "coords": int(info["has_coords"]), "k": int(p.shape[0]), "ends": int(ends.shape[0]),
+             "max_share": int(counts.max()) if counts.size else 0, "mode": mode, "bits": dist_bits}
+    return hashlib.sha1(json.dumps(shape, sort_keys=True).encode()).hexdigest()[:16]
+
+
+def _time_plan(G, pairs, opts, reps, stream, out):
+    import torch
+
+    plan = G.plan(pairs, stream=stream.cuda_stream, **opts)
+    best = float("inf")
+    res = None
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run(out.data_ptr())
+        e1.record(stream)
+        plan.sync()
+        if r > 0:
+            best = min(best, e0.elapsed_time(e1))
+    res = out.cpu().numpy().view(np.uint64).copy()
+    plan.close()
+    return best, res
+
+
+def tune(G: ppsp.Graph, pairs: np.ndarray, mode: str, base: dict | None = None, reps: int = 2,
+         budget_s: float = 60.0, log=None) -> dict:
+    """Coordinate descent over SPACE; returns the best option dict."""
+    import torch
+
+    pairs = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+    stream = torch.cuda.Stream()
+    out = torch.zeros(pairs.shape[0], dtype=torch.int64, device="cuda")
+    best = dict(base or {})
+    best.setdefault("mode", mode)
+    t_best, ref = _time_plan(G, pairs, best, reps, stream, out)
+    trials = [{"opts": dict(best), "ms": t_best}]
+    t0 = time.time()
+    for knob, values in SPACE:
+        for v in values:
+            if time.time() - t0 > budget_s:
+                break
+            if best.get(knob, None) == v or (knob not in best and v in (0, "auto", 512, "interleaved", 16)):
+                continue
+            cand = dict(best)
+            cand[knob] = v
+            try:
+                ms, res = _time_plan(G, pairs, cand, reps, stream, out)
+            except ppsp.PPSPError:
+                continue
+            if not np.array_equal(res, ref):
+                raise AssertionError(f"answers changed with {knob}={v}")
+            trials.append({"opts": dict(cand), "ms": ms})
+            if log:
+                log(json.dumps({"knob": knob, "value": v, "ms": round(ms, 3)}))
+            if ms < t_best * 0.97:
+                best, t_best = cand, ms
+    return {"opts": best, "ms": t_best, "trials": trials}
+
+
+def load_cache(path: str = CACHE) -> dict:
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        return json.load(f)
+
+
+def cached_or_tune(G: ppsp.Graph, pairs: np.ndarray, mode: str, dist_bits: int = 32, path: str = CACHE,
+                   allow_tune: bool = True, **kw) -> dict:
+    """Options for this (graph, batch, mode): from the cache, or tuned now and saved."""
+    sig = signature(G, pairs, mode, dist_bits)
+    cache = load_cache(path)
+    if sig in cache:
+        return cache[sig]["opts"]
+    if not allow_tune:
+        return {"mode": mode}
+    res = tune(G, pairs, mode, base={"mode": mode, "dist_bits": dist_bits}, **kw)
+    cache[sig] = {"opts": res["opts"], "ms": res["ms"]}
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    return res["opts"]

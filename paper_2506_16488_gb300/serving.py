@@ -1,0 +1,248 @@
+"""Continuous-batching query serving on one GPU.
+
+Requests (single queries or batches of pairs) arrive over time.  The
+scheduler packs waiting requests, oldest first, into micro-batches and starts
+one whenever an execution lane (a CUDA stream with its share of the GPU's
+CTAs) is free and the device memory the micro-batch's searches need fits the
+budget; finished micro-batches free their lane and memory immediately, so new
+arrivals join while earlier work is still on the device.  Each micro-batch is
+one plan (query graph of its pairs, Sec. 4.1; Multi-BiDS, Sec. 4.2) run by the
+persistent engine on a fraction of the SMs, so several micro-batches overlap
+on the device.  Answers never depend on how requests were packed (Theorems
+3.3/3.4: any schedule of the searches returns d(s,t)); `tests/` checks that
+each result is the same alone and in the mix.
+
+The scheduling core (:class:`Scheduler`) has no GPU dependency; the executor
+(:class:`GpuExecutor`) runs plans through the C ABI.
+"""
+
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import Callable, Optional
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    pairs: np.ndarray  # uint32 [k, 2]
+    arrival: float
+    start: Optional[float] = None
+    done: Optional[float] = None
+    result: Optional[np.ndarray] = None
+    status: int = 0
+
+
+@dataclass
+class MicroBatch:
+    requests: list
+    pairs: np.ndarray
+    bytes: int
+    lane: int
+    handle: object = None
+    started: float = 0.0
+
+
+class Scheduler:
+    """Admission and packing (no device code).
+
+    lanes        number of concurrent micro-batches
+    max_pairs    pairs per micro-batch (requests are never split)
+    budget       device bytes available for in-flight searches
+    bytes_for    callable(pairs) -> device bytes the micro-batch needs
+    """
+
+    def __init__(self, lanes: int, max_pairs: int, budget: int, bytes_for: Callable[[np.ndarray], int]):
+        assert lanes >= 1 and max_pairs >= 1
+        self.lanes = lanes
+        self.max_pairs = max_pairs
+        self.budget = budget
+        self.bytes_for = bytes_for
+        self.waiting: deque = deque()
+        self.free_lanes = list(range(lanes))
+        self.in_use = 0
+        self.rejected: list = []
+
+    def add(self, req: Request):
+        need = self.bytes_for(req.pairs)
+        if need > self.budget or req.pairs.shape[0] > self.max_pairs:
+            # can never be admitted in one piece: refuse instead of waiting forever
+            req.status = -1
+            self.rejected.append(req)
+            return
+        self.waiting.append(req)
+
+    def next_batch(self) -> Optional[MicroBatch]:
+        """Pack the oldest waiting requests that fit one lane and the memory budget."""
+        if not self.free_lanes or not self.waiting:
+            return None
+        reqs, k = [], 0
+        for req in list(self.waiting):
+            if k + req.pairs.shape[0] > self.max_pairs:
+                break
+            trial = np.concatenate([r.pairs for r in reqs] + [req.pairs])
+            if self.in_use + self.bytes_for(trial) > self.budget:
+                break
+            reqs.append(req)
+            k += req.pairs.shape[0]
+        if not reqs:
+            return None
+        for _ in reqs:
+            self.waiting.popleft()
+        pairs = np.concatenate([r.pairs for r in reqs])
+        mb = MicroBatch(reqs, pairs, self.bytes_for(pairs), self.free_lanes.pop(0))
+        self.in_use += mb.bytes
+        return mb
+
+    def finish(self, mb: MicroBatch):
+        self.in_use -= mb.bytes
+        self.free_lanes.append(mb.lane)
+        self.free_lanes.sort()
+
+
+def serve(arrivals: list, executor, scheduler: Scheduler, clock=time.perf_counter, poll_s: float = 2e-4) -> dict:
+    """Run requests arriving at the given times (seconds from start).
+
+    arrivals: list of (t_arrival, pairs) sorted by time.  Returns per-request
+    results and latencies, p50/p99 and sustained queries/sec.
+    """
+    reqs = [Request(i, np.ascontiguousarray(p, dtype=np.uint32).reshape(-1, 2), t) for i, (t, p) in
+            enumerate(arrivals)]
+    t0 = clock()
+    nxt = 0
+    running: list = []
+    finished = 0
+    total = len(reqs)
+    while finished + len(scheduler.rejected) < total:
+        now = clock() - t0
+        while nxt < total and reqs[nxt].arrival <= now:
+            scheduler.add(reqs[nxt])
+            nxt += 1
+        while True:
+            mb = scheduler.next_batch()
+            if mb is None:
+                break
+            for r in mb.requests:
+                r.start = clock() - t0
+            mb.started = clock() - t0
+            mb.handle = executor.start(mb.pairs, mb.lane)
+            running.append(mb)
+        for mb in list(running):
+            res = executor.poll(mb.handle)
+            if res is None:
+                continue
+            status, dists = res
+            end = clock() - t0
+            off = 0
+            for r in mb.requests:
+                k = r.pairs.shape[0]
+                r.result = dists[off:off + k]
+                r.status = status
+                r.done = end
+                off += k
+            finished += len(mb.requests)
+            scheduler.finish(mb)
+            running.remove(mb)
+        if not running and nxt < total and not scheduler.waiting:
+            # idle until the next arrival
+            wait = reqs[nxt].arrival - (clock() - t0)
+            if wait > 0:
+                time.sleep(min(wait, 0.01))
+        else:
+            time.sleep(poll_s)
+    span = max((r.done for r in reqs if r.done is not None), default=0.0)
+    lat = np.array([r.done - r.arrival for r in reqs if r.done is not None])
+    nq = sum(r.pairs.shape[0] for r in reqs if r.done is not None)
+    return {
+        "requests": reqs,
+        "latency_p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
+        "latency_p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
+        "queries": int(nq),
+        "span_s": float(span),
+        "qps": float(nq / span) if span > 0 else None,
+        "rejected": len(scheduler.rejected),
+    }
+
+
+def poisson_arrivals(rate_qps: float, duration_s: float, pair_source: Callable[[int], np.ndarray], seed: int,
+                     batch_sizes=(1, 1, 1, 4, 16, 64, 256)) -> list:
+    """Poisson request stream whose query rate is rate_qps: each request is a
+    single query or a batch (size drawn from batch_sizes)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.asarray(batch_sizes)
+    mean_size = sizes.mean()
+    req_rate = rate_qps / mean_size
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / req_rate)
+        if t > duration_s:
+            break
+        k = int(rng.choice(sizes))
+        out.append((t, pair_source(k)))
+    return out
+
+
+class GpuExecutor:
+    """Runs a micro-batch as one plan on a lane's stream with lane_ctas CTAs."""
+
+    def __init__(self, graph, lanes: int, mode: str = "bids", dist_bits: int = 32, lane_ctas: int = 0, **opts):
+        import torch
+
+        from . import ppsp
+
+        self.ppsp = ppsp
+        self.torch = torch
+        self.graph = graph
+        self.streams = [torch.cuda.Stream() for _ in range(lanes)]
+        self.mode = mode
+        self.dist_bits = dist_bits
+        self.lane_ctas = lane_ctas
+        self.opts = opts
+
+    def start(self, pairs: np.ndarray, lane: int):
+        s = self.streams[lane]
+        plan = self.graph.plan(pairs, mode=self.mode, dist_bits=self.dist_bits, stream=s.cuda_stream,
+                               max_ctas=self.lane_ctas, **self.opts)
+        out = self.torch.zeros(pairs.shape[0], dtype=self.torch.int64, device="cuda")
+        plan.run(out.data_ptr())
+        ev = self.torch.cuda.Event()
+        ev.record(s)
+        return (plan, out, ev)
+
+    def poll(self, handle):
+        plan, out, ev = handle
+        if not ev.query():
+            return None
+        try:
+            plan.sync()
+            status = 0
+        except self.ppsp.PPSPError as e:
+            status = e.status
+        d = out.cpu().numpy().view(np.uint64).copy()
+        plan.close()
+        return status, d
+
+
+def slot_bytes(n: int, searches_per_slot: int, dist_bits: int) -> int:
+    """Device bytes of one team's search memory (distances, two bitmaps, two
+    queues, touched list), as the library sizes it."""
+    flat = max(64, n * searches_per_slot)
+    flat = (flat + 63) // 64 * 64
+    qcap = min(flat, flat // 8 + 4096)
+    tcap = min(flat, flat // 4 + 4096)
+    return flat * dist_bits // 8 + 2 * (flat // 8) + 2 * 4 * qcap + 4 * tcap
+
+
+def memory_model(n: int, lane_ctas: int, dist_bits: int) -> Callable[[np.ndarray], int]:
+    """bytes_for(pairs): every team of the micro-batch holds one pair slot;
+    there are at most min(lane_ctas, queries) teams."""
+    per = slot_bytes(n, 2, dist_bits)
+
+    def f(pairs: np.ndarray) -> int:
+        return int(min(lane_ctas, max(1, pairs.shape[0])) * per)
+
+    return f

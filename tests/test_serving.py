@@ -1,0 +1,107 @@
+"""Serving: admission by memory and continuous batching (scheduler on CPU,
+results alone vs in the mix on the GPU)."""
+
+import time
+
+import numpy as np
+import pytest
+
+from paper_2506_16488_gb300.serving import Request, Scheduler, memory_model, poisson_arrivals, serve, slot_bytes
+
+
+def _req(i, k, t=0.0):
+    return Request(i, np.stack([np.arange(k), np.arange(k) + 1], axis=1).astype(np.uint32) + i * 1000, t)
+
+
+def test_scheduler_packs_oldest_first_within_limits():
+    sch = Scheduler(lanes=2, max_pairs=8, budget=100, bytes_for=lambda p: 10 * p.shape[0])
+    for i, k in enumerate([3, 4, 2, 5, 1]):
+        sch.add(_req(i, k))
+    a = sch.next_batch()  # 3 + 4 fit (7 pairs, 70 bytes); adding 2 would exceed 8 pairs
+    assert [r.rid for r in a.requests] == [0, 1] and a.bytes == 70 and a.lane == 0
+    b = sch.next_batch()  # 2 fits (20 bytes -> 90); 5 more would exceed the budget
+    assert [r.rid for r in b.requests] == [2] and b.lane == 1
+    assert sch.next_batch() is None  # no free lane
+    sch.finish(a)
+    c = sch.next_batch()
+    assert [r.rid for r in c.requests] == [3, 4] and sch.in_use == 20 + 60
+
+
+def test_scheduler_rejects_requests_that_can_never_fit():
+    sch = Scheduler(lanes=1, max_pairs=4, budget=30, bytes_for=lambda p: 10 * p.shape[0])
+    sch.add(_req(0, 5))   # more pairs than a micro-batch
+    sch.add(_req(1, 4))   # needs 40 bytes > budget
+    sch.add(_req(2, 2))
+    assert [r.rid for r in sch.rejected] == [0, 1]
+    assert [r.rid for r in sch.next_batch().requests] == [2]
+
+
+class FakeExecutor:
+    """Completes a micro-batch 2 ms after it starts; answer = s + t."""
+
+    def __init__(self):
+        self.live = 0
+        self.max_live = 0
+
+    def start(self, pairs, lane):
+        self.live += 1
+        self.max_live = max(self.max_live, self.live)
+        return (time.perf_counter() + 0.002, pairs)
+
+    def poll(self, h):
+        t, pairs = h
+        if time.perf_counter() < t:
+            return None
+        self.live -= 1
+        return 0, pairs[:, 0].astype(np.uint64) + pairs[:, 1]
+
+
+def test_serve_loop_continuous_batching_with_fake_executor():
+    rng = np.random.default_rng(0)
+    arrivals = poisson_arrivals(4000, 0.05, lambda k: rng.integers(0, 1000, size=(k, 2)), seed=1,
+                                batch_sizes=(1, 2, 8))
+    ex = FakeExecutor()
+    sch = Scheduler(lanes=3, max_pairs=16, budget=10 ** 9, bytes_for=lambda p: p.shape[0])
+    out = serve(arrivals, ex, sch)
+    assert ex.max_live <= 3 and out["rejected"] == 0
+    for (t, p), r in zip(arrivals, out["requests"]):
+        assert np.array_equal(r.result, p[:, 0].astype(np.uint64) + p[:, 1])
+        assert r.done >= r.arrival
+    assert out["latency_p99_ms"] >= out["latency_p50_ms"] > 0
+
+
+def test_memory_model_matches_slot_sizes():
+    f = memory_model(n=1000, lane_ctas=8, dist_bits=64)
+    per = slot_bytes(1000, 2, 64)
+    assert f(np.zeros((3, 2))) == 3 * per and f(np.zeros((100, 2))) == 8 * per
+    assert per >= 2 * 1000 * 8  # at least the two distance arrays
+
+
+@pytest.mark.gpu
+def test_serving_results_alone_equal_in_mix():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import oracle
+    from paper_2506_16488_gb300 import ppsp
+    from paper_2506_16488_gb300.serving import GpuExecutor
+    from workloads import random_pairs, road_like_graph
+
+    g = road_like_graph(96, seed=81)
+    rng = np.random.default_rng(82)
+    src = lambda k: g.lcc[rng.integers(0, g.lcc.shape[0], size=(k, 2))]
+    arrivals = poisson_arrivals(3000, 0.3, src, seed=83, batch_sizes=(1, 1, 4, 16, 64))
+    with ppsp.Graph.from_csr(g) as G:
+        lanes, lane_ctas = 3, 32
+        ex = GpuExecutor(G, lanes, mode="bidastar", dist_bits=64, lane_ctas=lane_ctas)
+        sch = Scheduler(lanes, 256, 2 ** 34, memory_model(g.n, lane_ctas, 64))
+        out = serve(arrivals, ex, sch)
+        assert out["rejected"] == 0
+        for r in out["requests"]:
+            assert r.status == 0
+            alone = G.batch(r.pairs, mode="bidastar", dist_bits=64)
+            assert np.array_equal(r.result, alone)
+        sample = np.concatenate([r.pairs for r in out["requests"][:20]])
+        want = oracle.pairs(g.offsets, g.targets, g.weights, sample)
+        got = np.concatenate([r.result for r in out["requests"][:20]])
+        assert np.array_equal(got, want)
