@@ -183,6 +183,11 @@ struct Smem {
     u64 bound[KMAX];
     PartnerDev pcache[PCAP];
     u32 pcached, pot_any;
+    // one-CTA bucketed frontier (run_local)
+    u64 lstep, lcur;
+    u64 lfar_min[2];
+    u32 lfar_n[2];
+    u32 lfar_fb, lfar_tgt, lspill, tov;
     // step scalars
     u64 minkey_in, minkey_acc;
     u32 count, overflow, dir0, dir1, tile, flag, total, nitems;
@@ -297,11 +302,18 @@ __device__ __forceinline__ PartnerDev partner(const EngineArgs& a, const Smem<B>
 // mu[qe] <- min(mu[qe], s); on improvement refresh mumax of both ends (Table 2,
 // Multi-PPSP: WriteMin(mumax[i], max_j mu[<q_i, q_j>])).
 template <int B>
-__device__ __forceinline__ void try_mu(const EngineArgs& a, const GroupDev& G, const Smem<B>& sm,
+__device__ __forceinline__ void try_mu(const EngineArgs& a, const GroupDev& G, Smem<B>& sm,
                                        u32 qe, u64 s) {
     if (s >= ldcg64(a.mu + qe)) return;
     u64 old = amin64(a.mu + qe, s);
-    if (s >= old || G.qcnt <= 1 || G.mode != GM_BIDIR) return;
+    if (s >= old) return;
+    if (G.qcnt <= 1 || G.mode != GM_BIDIR) {
+        // one query edge: the prune bound of every search is mu itself
+        // (shared-memory mirror, read by one-CTA teams)
+        atomicMin(reinterpret_cast<unsigned long long*>(&sm.bound[0]), (unsigned long long)s);
+        if (G.scnt == 2) atomicMin(reinterpret_cast<unsigned long long*>(&sm.bound[1]), (unsigned long long)s);
+        return;
+    }
     QEdgeDev e = a.qedges[qe];
     u32 ends[2] = {e.a, e.b};
 #pragma unroll
@@ -313,12 +325,13 @@ __device__ __forceinline__ void try_mu(const EngineArgs& a, const GroupDev& G, c
             m = mv > m ? mv : m;
         }
         amin64(a.mumax + G.sbeg + x, m);
+        atomicMin(reinterpret_cast<unsigned long long*>(&sm.bound[x]), (unsigned long long)m);
     }
 }
 
 // UpdateDistance for <v, i> at distance d (bidirectional family, generic groups)
 template <typename D, int B>
-__device__ __forceinline__ void update_bidir(const EngineArgs& a, GCtx<D>& c, const Smem<B>& sm,
+__device__ __forceinline__ void update_bidir(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm,
                                              u32 v, u32 i, u64 d) {
     const u32 pc = sm.pcnt[i];
     for (u32 p = 0; p < pc; ++p) {
@@ -533,6 +546,349 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
 }
 
 // ----------------------------------------------------------------------------
+// one-CTA teams: bucketed frontier in shared memory
+// ----------------------------------------------------------------------------
+// Delta*-stepping with buckets.  An entry <v, i> is stored with the distance it
+// was inserted with, in the bucket of the step whose threshold first covers its
+// key: bucket b = ceil(key / step), i.e. it is extracted at theta = b * step
+// (keys at or below the current threshold go to the next step).  Waiting
+// entries are therefore never re-read.  A later, smaller distance inserts a new
+// entry; the old one is recognised as stale at extraction (the stored distance
+// no longer matches) and dropped.  The ring holds the next LR_NB - 1 steps in
+// shared memory; entries further ahead go to a far list in the slot (re-bucketed
+// when the ring's window reaches them); an entry that finds its bucket or the
+// far list full sets its bit in the slot's spill bitmap and is recovered from
+// its current distance when nothing else is left.
+template <typename D>
+struct LR {
+    static constexpr u32 NB = 16;                          // buckets in the ring
+    static constexpr u32 CAP = sizeof(D) == 4 ? 512 : 256;  // entries per bucket
+    static constexpr size_t bytes() { return (size_t)NB * CAP * (4 + sizeof(D)) + NB * 4; }
+};
+
+template <typename D, int B>
+struct LocalView {
+    u32* rf;  // [NB * CAP] flat index
+    D* rd;    // [NB * CAP] distance at insertion
+    u32* rn;  // [NB] entries per bucket
+};
+
+template <typename D, int B>
+__device__ __forceinline__ LocalView<D, B> local_view(Smem<B>& sm) {
+    unsigned char* p = reinterpret_cast<unsigned char*>(&sm) + ((sizeof(Smem<B>) + 15) & ~(size_t)15);
+    LocalView<D, B> L;
+    L.rd = reinterpret_cast<D*>(p);
+    L.rf = reinterpret_cast<u32*>(p + (size_t)LR<D>::NB * LR<D>::CAP * sizeof(D));
+    L.rn = L.rf + LR<D>::NB * LR<D>::CAP;
+    return L;
+}
+
+template <typename D, int B>
+__device__ __forceinline__ void insert_local(GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L, u32 f, u32 i,
+                                             i64 key, u64 d) {
+    const u64 step = sm.lstep;
+    u64 b = ((u64)key + step - 1) / step;
+    const u64 cur = sm.lcur;
+    if (b <= cur) b = cur + 1;
+    bool stored = false;
+    if (b < cur + LR<D>::NB) {
+        const u32 s = (u32)(b % LR<D>::NB);
+        const u32 pos = atomicAdd(&L.rn[s], 1u);
+        if (pos < LR<D>::CAP) {
+            L.rf[s * LR<D>::CAP + pos] = f;
+            L.rd[s * LR<D>::CAP + pos] = (D)d;
+            stored = true;
+        }
+    } else {
+        const u32 fb = sm.lfar_tgt;
+        const u32 pos = atomicAdd(&sm.lfar_n[fb], 1u);
+        if (pos < c.slot.qcap) {
+            c.slot.q[fb][pos] = f;
+            reinterpret_cast<D*>(c.slot.fd[fb])[pos] = (D)d;
+            atomicMin(reinterpret_cast<unsigned long long*>(&sm.lfar_min[fb]), (unsigned long long)b);
+            stored = true;
+        }
+    }
+    if (!stored) {
+        const u32 bit = 1u << (f & 31u);
+        if (atomicOr(c.slot.bm[0] + (f >> 5), bit) & bit) return;  // already spilled
+        sm.lspill = 1;
+    }
+    ++c.c_p;
+    if (c.G.scnt == 2) atomicAdd(&sm.cnt_dir[i], 1u);
+}
+
+template <typename D, int B>
+__device__ __forceinline__ void touch_local(GCtx<D>& c, Smem<B>& sm, u32 f) {
+    ++c.c_t;
+    const u32 pos = atomicAdd(&sm.tn, 1u);
+    if (pos < c.slot.tcap)
+        c.slot.touched[pos] = f;
+    else
+        sm.tov = 1;
+}
+
+template <typename D, int B>
+__device__ __forceinline__ void relax_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L,
+                                            u32 i, u64 d, uint2 ew) {
+    const u32 v2 = ew.x;
+    const u64 nd = d + (u64)ew.y;
+    int2 pv2 = make_int2(0, 0);
+    if (sm.pot_any) pv2 = __ldg(a.g.pc + v2);
+    if (nd > DT<D>::MAXV) {
+        atomicOr(a.err, ERRB_OVERFLOW);
+        return;
+    }
+    u32 f2;
+    if (c.pair) {
+        u64 x0, x1;
+        ld_pair(c.dist, v2, x0, x1);
+        const u64 own = i ? x1 : x0, oth = i ? x0 : x1;
+        if (nd >= own) return;
+        f2 = (v2 << 1) | i;
+        const u64 old = amin_dist(c.dist + f2, nd);
+        if (nd >= old) return;
+        ++c.c_r;
+        if (old == DT<D>::INF) touch_local<D, B>(c, sm, f2);
+        if (oth != DT<D>::INF) try_mu(a, c.G, sm, c.G.qbeg, nd + oth);
+    } else {
+        f2 = flat_of(c.G, c.n, v2, i);
+        if (nd >= ld_dist(c.dist + f2)) return;
+        const u64 old = amin_dist(c.dist + f2, nd);
+        if (nd >= old) return;
+        ++c.c_r;
+        if (old == DT<D>::INF) touch_local<D, B>(c, sm, f2);
+        if (c.G.mode == GM_BIDIR)
+            update_bidir<D, B>(a, c, sm, v2, i, nd);
+        else if (c.G.mode != GM_SSSP && v2 == c.G.target)
+            try_mu(a, c.G, sm, c.G.qbeg, nd);
+    }
+    i64 key, pv;
+    key_pv<B>(a, c.G, sm, i, pv2, nd, key, pv);
+    if (pruned(pv, sm.bound[i])) return;
+    insert_local<D, B>(c, sm, L, f2, i, key, nd);
+}
+
+// mode 0: entries of the current bucket (extract); mode 1: far-list or spill
+// entries (re-bucket, nothing is expanded).  src_f / src_d hold the tile.
+template <typename D, int B>
+__device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L, u32 cnt,
+                              int mode) {
+    const u32 t = threadIdx.x;
+    u32 deg = 0;
+    if (t < cnt) {
+        const u32 f = sm.flat[t];
+        const u64 dins = sm.d[t];  // stored distance (INF: recover from the current one)
+        u32 v, i;
+        decode_flat(c.G, c.n, f, v, i);
+        const u32 b0 = __ldg(a.g.off + v);
+        const u32 b1 = (mode == 0) ? __ldg(a.g.off + v + 1) : b0;
+        int2 pv2 = make_int2(0, 0);
+        if (sm.pot_any) pv2 = __ldg(a.g.pc + v);
+        u64 d, oth = DT<D>::INF;
+        if (c.pair) {
+            u64 x0, x1;
+            ld_pair(c.dist, v, x0, x1);
+            d = i ? x1 : x0;
+            oth = i ? x0 : x1;
+        } else {
+            d = ld_dist(c.dist + f);
+        }
+        if (c.G.scnt == 2) atomicSub(&sm.cnt_dir[i], 1u);  // the stored entry is consumed
+        if (d != DT<D>::INF && (dins == DT<D>::INF || d == dins)) {
+            i64 key, pv;
+            key_pv<B>(a, c.G, sm, i, pv2, d, key, pv);
+            if (mode == 1) {
+                insert_local<D, B>(c, sm, L, f, i, key, d);  // into the ring window or back to far
+            } else {
+                if (c.pair) {
+                    if (oth != DT<D>::INF) try_mu(a, c.G, sm, c.G.qbeg, d + oth);
+                } else if (c.G.mode == GM_BIDIR) {
+                    update_bidir<D, B>(a, c, sm, v, i, d);
+                }
+                if (!pruned(pv, sm.bound[i])) {
+                    deg = b1 - b0;
+                    sm.beg[t] = b0;
+                    sm.si[t] = (unsigned char)i;
+                    sm.d[t] = d;
+                    ++c.c_x;
+                }
+            }
+        }
+    }
+    if (mode == 1) {
+        __syncthreads();
+        return;
+    }
+    u32 total;
+    const u32 excl = block_excl_scan<B>(deg, sm, &total);
+    sm.pre[t] = (t < cnt) ? excl : total;
+    __syncthreads();
+    for (u32 e = t; e < total; e += B) {
+        u32 lo = 0, hi = cnt;
+        while (hi - lo > 1) {
+            const u32 mid = (lo + hi) >> 1;
+            if (sm.pre[mid] <= e) lo = mid; else hi = mid;
+        }
+        const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
+        const uint2 ew = __ldg(a.g.edges + edge);
+        ++c.c_e;
+        relax_local<D, B>(a, c, sm, L, sm.si[lo], sm.d[lo], ew);
+    }
+    __syncthreads();
+}
+
+// Re-bucket every entry of the far list `fb` (relative to the current bucket);
+// survivors beyond the ring window go to the other far list.
+template <typename D, int B>
+__device__ void redistribute_far(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L) {
+    const u32 t = threadIdx.x;
+    const u32 fb = sm.lfar_fb, nb = fb ^ 1u;
+    const u32 n = min(sm.lfar_n[fb], c.slot.qcap);
+    if (t == 0) {
+        sm.lfar_tgt = nb;
+        sm.lfar_n[nb] = 0;
+        sm.lfar_min[nb] = INF64;
+    }
+    __syncthreads();
+    for (u32 base = 0; base < n; base += B) {
+        const u32 cnt = min((u32)B, n - base);
+        if (t < cnt) {
+            sm.flat[t] = __ldcg(c.slot.q[fb] + base + t);
+            sm.d[t] = (u64)__ldcg(reinterpret_cast<const D*>(c.slot.fd[fb]) + base + t);
+        }
+        __syncthreads();
+        process_local<D, B>(a, c, sm, L, cnt, 1);
+    }
+    if (t == 0) {
+        sm.lfar_fb = nb;
+        sm.lfar_n[fb] = 0;
+        sm.lfar_min[fb] = INF64;
+    }
+    __syncthreads();
+}
+
+// Recover spilled entries (their bits in the slot's spill bitmap) from their
+// current distances.
+template <typename D, int B>
+__device__ void recover_spill(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L,
+                              u32 nwords) {
+    const u32 t = threadIdx.x;
+    if (t == 0) sm.lspill = 0;
+    __syncthreads();
+    for (u32 wb = 0; wb < nwords; wb += B) {
+        const u32 w = wb + t;
+        u32 bits = 0;
+        if (w < nwords) {
+            bits = __ldcg(c.slot.bm[0] + w);
+            if (bits) c.slot.bm[0][w] = 0u;
+        }
+        u32 total;
+        u32 idx = block_excl_scan<B>(__popc(bits), sm, &total);
+        for (u32 base = 0; base < total; base += B) {
+            while (bits && idx < base + B) {
+                const u32 bb = __ffs(bits) - 1;
+                bits &= bits - 1;
+                sm.flat[idx - base] = (w << 5) | bb;
+                sm.d[idx - base] = DT<D>::INF;
+                ++idx;
+            }
+            __syncthreads();
+            process_local<D, B>(a, c, sm, L, min((u32)B, total - base), 1);
+        }
+    }
+}
+
+// The stepping loop of one group on one CTA.  Returns the number of steps.
+template <typename D, int B>
+__device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nwords) {
+    const u32 t = threadIdx.x;
+    const LocalView<D, B> L = local_view<D, B>(sm);
+    const GroupDev& G = c.G;
+    for (u32 k = t; k < LR<D>::NB; k += B) L.rn[k] = 0;
+    if (t == 0) {
+        sm.lstep = (G.mode == GM_BIDIR) ? 2 * G.delta : G.delta;
+        sm.lcur = 0;
+        sm.lfar_fb = 0;
+        sm.lfar_tgt = 0;
+        sm.lfar_n[0] = sm.lfar_n[1] = 0;
+        sm.lfar_min[0] = sm.lfar_min[1] = INF64;
+        sm.lspill = 0;
+        sm.cnt_dir[0] = sm.cnt_dir[1] = 0;
+    }
+    __syncthreads();
+    // Init: the sources (key 0) go to the first step
+    if (t < G.scnt) insert_local<D, B>(c, sm, L, flat_of(G, c.n, sm.src[t], t), t, 0, 0);
+    __syncthreads();
+    u64 rounds = 0;
+    for (;;) {
+        // choose the next bucket (thread 0), moving far entries into the window
+        // when they are due soon or the ring is empty
+        if (t == 0) {
+            sm.flag = 0;  // 0 = process lcur, 1 = redistribute, 2 = recover, 3 = done
+            const u64 cur = sm.lcur;
+            u64 rb = INF64;
+            for (u32 j = 1; j < LR<D>::NB; ++j)
+                if (L.rn[(u32)((cur + j) % LR<D>::NB)] != 0) {
+                    rb = cur + j;
+                    break;
+                }
+            const u32 fb = sm.lfar_fb;
+            const u64 fm = sm.lfar_n[fb] ? sm.lfar_min[fb] : INF64;
+            bool stop = false;
+            if (G.scnt == 2 && G.mode == GM_BIDIR && sm.bound[0] == INF64 &&
+                (sm.cnt_dir[0] == 0 || sm.cnt_dir[1] == 0))
+                stop = true;  // App. B: one side ran dry before mu was set
+            if (stop) {
+                sm.flag = 3;
+            } else if (fm != INF64 && (fm <= rb || fm < cur + LR<D>::NB / 2)) {
+                if (fm <= rb && fm > cur + 1) sm.lcur = fm - 1;
+                sm.flag = 1;
+            } else if (rb != INF64) {
+                sm.lcur = rb;
+            } else if (sm.lspill) {
+                sm.flag = 2;
+            } else {
+                sm.flag = 3;
+            }
+        }
+        __syncthreads();
+        const u32 what = sm.flag;
+        __syncthreads();
+        if (what == 3) break;
+        if (what == 1) {
+            redistribute_far<D, B>(a, c, sm, L);
+            continue;
+        }
+        if (what == 2) {
+            recover_spill<D, B>(a, c, sm, L, nwords);
+            continue;
+        }
+        // process bucket lcur: theta = lcur * step
+        ++rounds;
+        const u32 s = (u32)(sm.lcur % LR<D>::NB);
+        const u32 n = min(L.rn[s], LR<D>::CAP);
+        for (u32 base = 0; base < n; base += B) {
+            const u32 cnt = min((u32)B, n - base);
+            if (t < cnt) {
+                sm.flat[t] = L.rf[s * LR<D>::CAP + base + t];
+                sm.d[t] = (u64)L.rd[s * LR<D>::CAP + base + t];
+            }
+            __syncthreads();
+            process_local<D, B>(a, c, sm, L, cnt, 0);
+        }
+        if (t == 0) L.rn[s] = 0;
+        __syncthreads();
+    }
+    // entries left behind by the disconnected exit: clear the ring and spills
+    if (sm.lspill) {
+        for (u32 w = t; w < nwords; w += B) c.slot.bm[0][w] = 0u;
+    }
+    __syncthreads();
+    return rounds;
+}
+
+// ----------------------------------------------------------------------------
 // paths: meeting vertex, then a warp walks tight edges back to each source
 // ----------------------------------------------------------------------------
 // Walk from x0 towards the source of search i along edges (u, x) with
@@ -689,12 +1045,17 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
 
     // Init (Table 2): delta_i[q_i] = 0 and <q_i, i> in F for every search;
     // mu = inf (0 when both ends coincide).
+    // one-CTA teams keep the frontier in shared memory (run_local); the
+    // policies SPARSE and DENSE force the global queue / bitmap path
+    const bool local = (tc.size == 1) && (a.frontier == PPSP_FRONTIER_AUTO) && !tc.global_bar;
     if (tc.rank == 0) {
         if (t < G.scnt) {
             const u32 f = flat_of(G, c.n, sm.src[t], t);
             st_dist(c.dist + f, 0);
-            atomicOr(slot.bm[0] + (f >> 5), 1u << (f & 31u));
-            slot.q[0][t] = f;
+            if (!local) {
+                atomicOr(slot.bm[0] + (f >> 5), 1u << (f & 31u));
+                slot.q[0][t] = f;
+            }
             slot.touched[t] = f;
         }
         for (u32 q = t; q < G.qcnt; q += B) {
@@ -745,7 +1106,32 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
     u64 rounds = 0, dense_rounds = 0;
     u32 exit_count = 0, exit_bcur = 0;
     bool exit_dense = false;
-    for (;; ++r) {
+    // prune bounds (the shared-memory mirror one-CTA teams read)
+    if (t < G.scnt) {
+        u64 b;
+        if (G.mode == GM_BIDIR)
+            b = (G.qcnt == 1) ? ldcg64(a.mu + G.qbeg) : ldcg64(a.mumax + G.sbeg + t);
+        else if (G.mode == GM_SSSP)
+            b = INF64;
+        else
+            b = ldcg64(a.mu + G.qbeg);
+        sm.bound[t] = b;
+    }
+    if (local) {
+        if (t == 0) {
+            sm.tn = G.scnt;  // touched entries so far: the sources
+            sm.tov = 0;
+        }
+        __syncthreads();
+        rounds = run_local<D, B>(a, c, sm, nwords);
+        if (t == 0) {
+            slot.st->touched_n = sm.tn;
+            slot.st->touched_overflow = sm.tov;
+            sm.tn = 0;
+        }
+        __syncthreads();
+    }
+    for (; !local; ++r) {
         const u32 cur = r % 3, nxt = (r + 1) % 3, old = (r + 2) % 3;
         const u32 bcur = r & 1u, bnxt = bcur ^ 1u;
         if (t == 0) {
@@ -901,8 +1287,14 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
 }
 
 template <typename D, int B>
+constexpr size_t engine_smem_bytes() {
+    return ((sizeof(Smem<B>) + 15) & ~(size_t)15) + LR<D>::bytes();
+}
+
+template <typename D, int B>
 __global__ void __launch_bounds__(B) engine_kernel(EngineArgs a) {
-    __shared__ Smem<B> sm;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<B>& sm = *reinterpret_cast<Smem<B>*>(smem_raw);
     TeamCtx tc;
     tc.team = a.cta_team[blockIdx.x];
     tc.rank = blockIdx.x - a.team_first[tc.team];
@@ -949,11 +1341,24 @@ __global__ void __launch_bounds__(B) engine_kernel(EngineArgs a) {
 // host side
 // ----------------------------------------------------------------------------
 template <typename D, int B>
+static ppsp_status set_smem_attr() {
+    static bool done = false;  // per instantiation; the attribute is per device function
+    if (!done) {
+        PPSP_CUDA_TRY(cudaFuncSetAttribute(engine_kernel<D, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)engine_smem_bytes<D, B>()));
+        done = true;
+    }
+    return PPSP_OK;
+}
+
+template <typename D, int B>
 static ppsp_status launch_t(const EngineArgs& a, u32 grid, cudaStream_t stream) {
+    ppsp_status st = set_smem_attr<D, B>();
+    if (st != PPSP_OK) return st;
     EngineArgs args = a;
     void* params[] = {&args};
     PPSP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)engine_kernel<D, B>, dim3(grid), dim3(B),
-                                              params, 0, stream));
+                                              params, engine_smem_bytes<D, B>(), stream));
     return PPSP_OK;
 }
 
@@ -973,7 +1378,10 @@ ppsp_status launch_engine(const EngineArgs& a, int dist_bits, int block_threads,
 
 template <typename D, int B>
 static ppsp_status occ_t(int* bpsm) {
-    PPSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bpsm, engine_kernel<D, B>, B, 0));
+    ppsp_status st = set_smem_attr<D, B>();
+    if (st != PPSP_OK) return st;
+    PPSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bpsm, engine_kernel<D, B>, B,
+                                                                engine_smem_bytes<D, B>()));
     return PPSP_OK;
 }
 

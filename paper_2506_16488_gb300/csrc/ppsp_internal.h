@@ -94,7 +94,8 @@ struct SlotState {
 struct SlotDev {
     void* dist;           // tentative distances, flat_cap entries of DistT
     u32* bm[2];           // frontier bitmaps, flat_cap bits each
-    u32* q[2];            // frontier queues, qcap entries each
+    u32* q[2];            // frontier queues (one-CTA teams: far lists), qcap entries each
+    void* fd[2];          // one-CTA teams: distance stored with each far-list entry
     u32* touched;         // flat indices that left infinity, tcap entries
     SlotState* st;
     u64 flat_cap;         // k_cap * n

@@ -288,3 +288,43 @@ def test_plan_replays_a_cuda_graph(cfg1):
         assert np.array_equal(dst.cpu().numpy().view(np.uint64), want)
         assert plan.uses_graph()
     plan.close()
+
+
+@pytest.mark.parametrize("delta", [1, 3, 0, 5000, 10 ** 7])
+def test_one_cta_bucket_frontier_delta_sweep(cfg1, delta):
+    g, pairs, want, G = cfg1
+    for mode in ("bids", "bidastar", "et", "astar"):
+        for bits in (32, 64):
+            got = G.batch(pairs, mode=mode, delta=delta, team_ctas=1, dist_bits=bits)
+            assert np.array_equal(got, want), (mode, bits)
+
+
+@pytest.mark.parametrize("delta", [1, 0, 10 ** 9])
+def test_one_cta_far_list_and_spills(delta):
+    # Delta = 1 sends most entries to the far list; a huge Delta puts whole
+    # frontiers into one bucket, overflowing it into the spill bitmap.
+    g = road_like_graph(160, seed=91)
+    pairs = np.concatenate([random_pairs(g, 40, 92), clique_pairs(g, 5, 93)])
+    want = oracle.pairs(g.offsets, g.targets, g.weights, pairs)
+    with ppsp.Graph.from_csr(g) as G:
+        for mode in ("bids", "bidastar"):
+            for bits in (32, 64):
+                got = G.batch(pairs, mode=mode, delta=delta, team_ctas=1, big_team_ctas=1, dist_bits=bits)
+                assert np.array_equal(got, want), (mode, bits)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tiny_random_graphs_one_cta(seed):
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(2, 40))
+    off, tgt, w = _random_graph(rng, n, int(rng.integers(0, 3 * n + 1)), 1000, zero_frac=0.2)
+    coords = rng.uniform(0, 10, size=(n, 2)).astype(np.float32)
+    fw = oracle.floyd_warshall(off, tgt, w)
+    pairs = np.array([(s, t) for s in range(n) for t in range(n)], dtype=np.uint32)
+    want = fw[pairs[:, 0], pairs[:, 1]]
+    with ppsp.Graph(off, tgt, w, coords) as G:
+        for mode in ("bids", "bidastar", "et", "astar"):
+            for strategy in ("multi", "plain_star"):
+                got = G.batch(pairs, mode=mode, strategy=strategy, team_ctas=1, big_team_ctas=1,
+                              delta=int(rng.integers(1, 3000)))
+                assert np.array_equal(got, want), (mode, strategy)
