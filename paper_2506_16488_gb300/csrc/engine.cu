@@ -184,13 +184,13 @@ struct Smem {
     PartnerDev pcache[PCAP];
     u32 pcached, pot_any;
     // one-CTA bucketed frontier (run_local)
-    u64 lstep, lcur;
+    u64 lstep, lcur, llate;
     u64 lfar_min[2];
     u32 lfar_n[2];
     u32 lfar_fb, lfar_tgt, lspill, tov;
     // step scalars
     u64 minkey_in, minkey_acc;
-    u32 count, overflow, dir0, dir1, tile, flag, total, nitems;
+    u32 count, overflow, dir0, dir1, tile, flag, total, nitems, cert;
     u32 cnt_dir[2];
     u32 group;
     u64 mu0;
@@ -589,7 +589,12 @@ __device__ __forceinline__ void insert_local(GCtx<D>& c, Smem<B>& sm, const Loca
     const u64 step = sm.lstep;
     u64 b = ((u64)key + step - 1) / step;
     const u64 cur = sm.lcur;
-    if (b <= cur) b = cur + 1;
+    if (b <= cur) {
+        // already under the threshold: due at the next step; remember the key
+        // (the bucket's lower bound (b - 1) * step does not hold for it)
+        b = cur + 1;
+        atomicMin(reinterpret_cast<unsigned long long*>(&sm.llate), (unsigned long long)key);
+    }
     bool stored = false;
     if (b < cur + LR<D>::NB) {
         const u32 s = (u32)(b % LR<D>::NB);
@@ -598,6 +603,14 @@ __device__ __forceinline__ void insert_local(GCtx<D>& c, Smem<B>& sm, const Loca
             L.rf[s * LR<D>::CAP + pos] = f;
             L.rd[s * LR<D>::CAP + pos] = (D)d;
             stored = true;
+        } else {
+            // the bucket continues in its global overflow region
+            const u32 ob = c.slot.ocap / LR<D>::NB, p2 = pos - LR<D>::CAP;
+            if (p2 < ob) {
+                c.slot.of[s * ob + p2] = f;
+                reinterpret_cast<D*>(c.slot.od)[s * ob + p2] = (D)d;
+                stored = true;
+            }
         }
     } else {
         const u32 fb = sm.lfar_tgt;
@@ -814,6 +827,7 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
         sm.lfar_n[0] = sm.lfar_n[1] = 0;
         sm.lfar_min[0] = sm.lfar_min[1] = INF64;
         sm.lspill = 0;
+        sm.llate = INF64;
         sm.cnt_dir[0] = sm.cnt_dir[1] = 0;
     }
     __syncthreads();
@@ -839,8 +853,21 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
             if (G.scnt == 2 && G.mode == GM_BIDIR && sm.bound[0] == INF64 &&
                 (sm.cnt_dir[0] == 0 || sm.cnt_dir[1] == 0))
                 stop = true;  // App. B: one side ran dry before mu was set
+            // mu certificate: every stored entry has key > (next bucket - 1) * step,
+            // and a prune value >= its key; once that reaches the largest prune
+            // bound of the group, every remaining entry would be pruned.
+            const u64 nextb = rb < fm ? rb : fm;
+            if (!stop && !sm.lspill && nextb != INF64 && G.mode != GM_SSSP) {
+                u64 bmax = 0;
+                for (u32 i = 0; i < G.scnt; ++i) bmax = sm.bound[i] > bmax ? sm.bound[i] : bmax;
+                u64 lb = (nextb - 1) * sm.lstep + 1;  // keys in buckets >= nextb
+                if (nextb == cur + 1 && sm.llate < lb) lb = sm.llate;
+                if (bmax != INF64 && bmax > 0 && lb >= bmax) stop = true;
+            }
             if (stop) {
                 sm.flag = 3;
+            } else if (sm.lspill) {
+                sm.flag = 2;  // recover spilled entries before they fall behind
             } else if (fm != INF64 && (fm <= rb || fm < cur + LR<D>::NB / 2)) {
                 if (fm <= rb && fm > cur + 1) sm.lcur = fm - 1;
                 sm.flag = 1;
@@ -866,13 +893,22 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
         }
         // process bucket lcur: theta = lcur * step
         ++rounds;
+        if (t == 0) sm.llate = INF64;
+        __syncthreads();
         const u32 s = (u32)(sm.lcur % LR<D>::NB);
-        const u32 n = min(L.rn[s], LR<D>::CAP);
+        const u32 ob = c.slot.ocap / LR<D>::NB;
+        const u32 n = min(L.rn[s], LR<D>::CAP + ob);
         for (u32 base = 0; base < n; base += B) {
             const u32 cnt = min((u32)B, n - base);
             if (t < cnt) {
-                sm.flat[t] = L.rf[s * LR<D>::CAP + base + t];
-                sm.d[t] = (u64)L.rd[s * LR<D>::CAP + base + t];
+                const u32 k = base + t;
+                if (k < LR<D>::CAP) {
+                    sm.flat[t] = L.rf[s * LR<D>::CAP + k];
+                    sm.d[t] = (u64)L.rd[s * LR<D>::CAP + k];
+                } else {
+                    sm.flat[t] = __ldcg(c.slot.of + s * ob + (k - LR<D>::CAP));
+                    sm.d[t] = (u64)__ldcg(reinterpret_cast<const D*>(c.slot.od) + s * ob + (k - LR<D>::CAP));
+                }
             }
             __syncthreads();
             process_local<D, B>(a, c, sm, L, cnt, 0);
@@ -1076,6 +1112,8 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
             S[0].overflow = 0;
             S[0].cnt_dir[0] = 1;
             S[0].cnt_dir[1] = G.scnt == 2 ? 1 : 0;
+            S[0].bmax = INF64;
+            S[1].bmax = INF64;
             S[1].count = 0;
             S[1].minkey = INF64;
             S[1].tile = 0;
@@ -1141,12 +1179,15 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
             sm.dir0 = ld_volatile(&S[cur].cnt_dir[0]);
             sm.dir1 = ld_volatile(&S[cur].cnt_dir[1]);
             sm.mu0 = ldcg64(a.mu + G.qbeg);
+            sm.cert = (u32)(ldcg64(&S[cur].bmax) <= sm.minkey_in && G.mode != GM_SSSP);
         }
         __syncthreads();
         const u32 count = sm.count;
         const u64 minkey = sm.minkey_in;
         dense_cur = dense_cur || sm.overflow != 0;
-        bool stop = (count == 0);
+        // mu certificate: every entry's prune value >= its key >= minkey >= the
+        // largest bound (snapshotted by the team leader before the barrier)
+        bool stop = (count == 0) || (sm.cert != 0);
         // App. B: a two-search group whose one side ran dry before mu was ever
         // set is disconnected.
         if (!stop && G.mode == GM_BIDIR && G.scnt == 2 && sm.mu0 == INF64 &&
@@ -1178,6 +1219,7 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
             S[old].tile = 0;
             S[old].overflow = 0;
             S[old].cnt_dir[0] = S[old].cnt_dir[1] = 0;
+            S[old].bmax = INF64;
         }
         if (t == 0) {
             sm.minkey_acc = INF64;
@@ -1235,6 +1277,20 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
         }
         // flush per-CTA step results
         __syncthreads();
+        if (t == 0 && tc.rank == 0) {
+            u64 bmax = 0;
+            for (u32 i = 0; i < G.scnt && bmax != INF64; ++i) {
+                u64 b;
+                if (G.mode == GM_BIDIR)
+                    b = (G.qcnt == 1) ? ldcg64(a.mu + G.qbeg) : ldcg64(a.mumax + G.sbeg + i);
+                else if (G.mode == GM_SSSP)
+                    b = INF64;
+                else
+                    b = ldcg64(a.mu + G.qbeg);
+                bmax = b > bmax ? b : bmax;
+            }
+            S[nxt].bmax = (bmax == 0) ? INF64 : bmax;
+        }
         if (t == 0) {
             if (sm.minkey_acc != INF64)
                 amin64(&S[nxt].minkey, sm.minkey_acc);

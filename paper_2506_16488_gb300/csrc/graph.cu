@@ -163,9 +163,11 @@ ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u
     const u64 W = dist_bits / 8;
     const u64 words = (flat_cap + 31) / 32;
     auto al = [](u64 x) { return (x + 255) & ~255ull; };
+    const u64 ocap = std::max<u64>(16 * 256, flat_cap / 4) / 16 * 16;
     const u64 b_dist = al(flat_cap * W), b_bm = al(words * 4), b_q = al((u64)qcap * 4),
-              b_fd = al((u64)qcap * W), b_t = al((u64)tcap * 4), b_st = al(sizeof(SlotState));
-    s->bytes = b_dist + 2 * b_bm + 2 * b_q + 2 * b_fd + b_t + b_st;
+              b_fd = al((u64)qcap * W), b_t = al((u64)tcap * 4), b_st = al(sizeof(SlotState)),
+              b_of = al(ocap * 4), b_od = al(ocap * W);
+    s->bytes = b_dist + 2 * b_bm + 2 * b_q + 2 * b_fd + b_t + b_st + b_of + b_od;
     cudaError_t e = cudaMalloc(&s->base, s->bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -186,6 +188,11 @@ ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u
     p += b_fd;
     s->dev.fd[1] = p;
     p += b_fd;
+    s->dev.of = (u32*)p;
+    p += b_of;
+    s->dev.od = p;
+    p += b_od;
+    s->dev.ocap = (u32)ocap;
     s->dev.touched = (u32*)p;
     p += b_t;
     s->dev.st = (SlotState*)p;

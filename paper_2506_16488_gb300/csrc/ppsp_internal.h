@@ -82,6 +82,7 @@ struct StepState {
     u32 overflow;         // queue overflowed: step must be processed from the bitmap
     u32 cnt_dir[2];       // entries per direction (two-search groups)
     u32 pad;
+    u64 bmax;             // largest prune bound of the group, taken before the step's barrier
 };
 
 struct SlotState {
@@ -96,6 +97,9 @@ struct SlotDev {
     u32* bm[2];           // frontier bitmaps, flat_cap bits each
     u32* q[2];            // frontier queues (one-CTA teams: far lists), qcap entries each
     void* fd[2];          // one-CTA teams: distance stored with each far-list entry
+    u32* of;              // one-CTA teams: bucket overflow (flat index), ocap entries
+    void* od;             //   and the stored distances
+    u32 ocap;             //   ocap / 16 entries per ring bucket
     u32* touched;         // flat indices that left infinity, tcap entries
     SlotState* st;
     u64 flat_cap;         // k_cap * n
