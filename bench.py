@@ -247,7 +247,7 @@ def run_ours(args):
         workload += f", at most {args.max_ctas} CTAs"
     G = ppsp.Graph.from_csr(g)
     stream = torch.cuda.Stream()
-    opts = dict(mode=mode, strategy="multi", stream=stream.cuda_stream, max_ctas=args.max_ctas)
+    opts = dict(mode=mode, strategy="multi", stream=stream.cuda_stream, max_ctas=args.max_ctas, cuda_graph=True)
     delta_rule = "default (mean edge weight)"
     model = None
     if args.delta:
@@ -286,6 +286,7 @@ def run_ours(args):
         ev[i][1].record(stream)
         counters.append(plan.sync())
     torch.cuda.synchronize()
+    plan_used_graph = plan.uses_graph()
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -326,9 +327,21 @@ def run_ours(args):
         return {"value": k / (ms / 1000.0), "unit": "queries/s", "ms": ms,
                 "gteps": pc["edges"] / (ms / 1000.0) / 1e9, "rounds": pc["rounds"]}
 
-    plain = run_plain(delta=args.delta or default_delta)
+    # the plain baseline gets its best team size (fewer CTAs make the
+    # per-step grid barrier cheaper; more give a step more parallelism)
+    def best_plain(**popts):
+        runs = []
+        for tc in args.plain_teams:
+            r = run_plain(team_ctas=tc, **popts)
+            r["team_ctas"] = tc if tc else "all resident CTAs"
+            runs.append(r)
+        best = max(runs, key=lambda r: r["value"])
+        best["tried"] = [{"team_ctas": r["team_ctas"], "value": r["value"]} for r in runs]
+        return best
+
+    plain = best_plain(delta=args.delta or default_delta)
     plain["delta"] = f"default {default_delta}" if not args.delta else f"fixed {args.delta}"
-    plain_same = run_plain(**({"delta": args.delta} if args.delta else {}))
+    plain_same = best_plain(**({"delta": args.delta} if args.delta else {}))
     plain_same["delta"] = delta_rule
 
     if rank != 0:
@@ -371,7 +384,8 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": alg_bytes},
         "e2e": {"value": world * k / (float(np.median(e2e_ms)) / 1000.0), "unit": "queries/s",
                 "h2d_bytes_per_step": int(pairs.nbytes), "d2h_bytes_per_step": int(k * 8)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (3 if model is not None else 2) * args.steps,
+        "cuda_graph": plan_used_graph,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
@@ -449,6 +463,8 @@ def main():
     ap.add_argument("--delta", type=int, default=0)
     ap.add_argument("--no-learned", action="store_true", help="use the default Delta, not the learned model")
     ap.add_argument("--queries", type=int, default=0, help="strided subset of the batch (profiling)")
+    ap.add_argument("--plain-teams", type=int, nargs="*", default=[16, 64, 0],
+                    help="team sizes tried for the plain one-query-at-a-time baseline (0 = all CTAs)")
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on resident CTAs (profiling)")
     ap.add_argument("--rates", type=float, nargs="*", default=[1000, 5000, 20000, 50000],
                     help="serving (config 5): offered query rates")

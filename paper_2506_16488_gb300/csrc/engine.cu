@@ -188,6 +188,7 @@ struct Smem {
     u64 lfar_min[2];
     u32 lfar_n[2];
     u32 lfar_fb, lfar_tgt, lspill, tov;
+    u32 lrecov, lidle;  // spill recovered since the last processed bucket; decisions without one
     // step scalars
     u64 minkey_in, minkey_acc;
     u32 count, overflow, dir0, dir1, tile, flag, total, nitems, cert;
@@ -828,6 +829,8 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
         sm.lfar_min[0] = sm.lfar_min[1] = INF64;
         sm.lspill = 0;
         sm.llate = INF64;
+        sm.lrecov = 0;
+        sm.lidle = 0;
         sm.cnt_dir[0] = sm.cnt_dir[1] = 0;
     }
     __syncthreads();
@@ -866,8 +869,11 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
             }
             if (stop) {
                 sm.flag = 3;
-            } else if (sm.lspill) {
-                sm.flag = 2;  // recover spilled entries before they fall behind
+            } else if (sm.lspill && (!sm.lrecov || (rb == INF64 && fm == INF64))) {
+                // recover spilled entries before they fall behind, at most once
+                // between two processed buckets (re-spilled entries wait for
+                // the bucket in front of them to be processed first)
+                sm.flag = 2;
             } else if (fm != INF64 && (fm <= rb || fm < cur + LR<D>::NB / 2)) {
                 if (fm <= rb && fm > cur + 1) sm.lcur = fm - 1;
                 sm.flag = 1;
@@ -878,6 +884,18 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
             } else {
                 sm.flag = 3;
             }
+        }
+        if (t == 0) {
+            // a bounded number of decisions without processing a bucket: the
+            // ring always gains entries from a redistribution or a recovery,
+            // so this only trips on an internal error, never on valid input
+            sm.lidle = (sm.flag == 1 || sm.flag == 2) ? sm.lidle + 1 : 0;
+            if (sm.lidle > 4096) {
+                atomicOr(a.err, ERRB_INTERNAL);
+                sm.flag = 3;
+            }
+            if (sm.flag == 2) sm.lrecov = 1;
+            if (sm.flag == 0) sm.lrecov = 0;
         }
         __syncthreads();
         const u32 what = sm.flag;

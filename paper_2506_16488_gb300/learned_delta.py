@@ -26,16 +26,20 @@ from . import ppsp
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS_DIR = os.path.join(HERE, "weights")
-GRID = tuple(range(-6, 3))  # log2(Delta / Delta_default)
+GRID = tuple(range(-12, 4))  # log2(Delta / Delta_default) the sweep may visit
 
 
 def weights_path(mode: str) -> str:
     return os.path.join(WEIGHTS_DIR, f"delta_{mode}.bin")
 
 
-def sweep(G: ppsp.Graph, pairs: np.ndarray, mode: str, grid=GRID, stream=None, reps: int = 1, **opts):
-    """Time every group of the batch at each grid point.
+def sweep(G: ppsp.Graph, pairs: np.ndarray, mode: str, grid=GRID, stream=None, reps: int = 1,
+          patience: int = 2, **opts):
+    """Time every group of the batch for Delta = Delta_default * 2^j.
 
+    Like the paper's doubling search (Sec. 6.1) the sweep starts at j = 0 and
+    walks down, then up, while the batch's total time improves (stopping after
+    `patience` worse points).  Grid points it never visits get time +inf.
     Returns (features [groups, 12], times_ns [groups, len(grid)], default_delta).
     """
     import torch
@@ -43,12 +47,15 @@ def sweep(G: ppsp.Graph, pairs: np.ndarray, mode: str, grid=GRID, stream=None, r
     default = max(1, int(round(G.info()["w_mean"])))
     s = stream or torch.cuda.Stream()
     out = torch.zeros(pairs.shape[0], dtype=torch.int64, device="cuda")
-    feats, times, ref = None, [], None
-    for j in grid:
+    grid = list(grid)
+    cols = {}
+    state = {"feats": None, "ref": None}
+
+    def run(j):
         delta = max(1, int(round(default * 2.0 ** j)))
         plan = G.plan(pairs, mode=mode, delta=delta, stream=s.cuda_stream, **opts)
-        if feats is None:
-            feats = plan.features()
+        if state["feats"] is None:
+            state["feats"] = plan.features()
         best = None
         for _ in range(reps + 1):  # first run warms up
             plan.run(out.data_ptr())
@@ -56,13 +63,30 @@ def sweep(G: ppsp.Graph, pairs: np.ndarray, mode: str, grid=GRID, stream=None, r
             t = plan.group_times().astype(np.float64)
             best = t if best is None else np.minimum(best, t)
         res = out.cpu().numpy().copy()
-        if ref is None:
-            ref = res
-        elif not np.array_equal(ref, res):  # Delta must not change answers
+        if state["ref"] is None:
+            state["ref"] = res
+        elif not np.array_equal(state["ref"], res):  # Delta must not change answers
             raise AssertionError(f"answers changed with delta={delta}")
-        times.append(best)
         plan.close()
-    return feats, np.stack(times, axis=1), default
+        cols[j] = best
+        return best.sum()
+
+    j0 = grid.index(0)
+    best_total = run(0)
+    for direction in (-1, 1):
+        worse, k = 0, j0 + direction
+        while 0 <= k < len(grid) and worse < patience:
+            tot = run(grid[k])
+            if tot < best_total:
+                best_total, worse = tot, 0
+            else:
+                worse += 1
+            k += direction
+    ng = state["feats"].shape[0]
+    times = np.full((ng, len(grid)), np.inf)
+    for j, col in cols.items():
+        times[:, grid.index(j)] = col
+    return state["feats"], times, default
 
 
 def labels_from_times(times: np.ndarray, grid=GRID) -> np.ndarray:
@@ -70,7 +94,10 @@ def labels_from_times(times: np.ndarray, grid=GRID) -> np.ndarray:
 
 
 def regret(times: np.ndarray, y_pred: np.ndarray, grid=GRID) -> float:
-    g = np.asarray(grid, dtype=np.float64)
+    """Time at the measured grid point nearest each prediction over the best."""
+    ok = _finite_cols(times)
+    g = np.asarray(grid, dtype=np.float64)[ok]
+    times = times[:, ok]
     idx = np.abs(np.clip(y_pred, g[0], g[-1])[:, None] - g[None, :]).argmin(axis=1)
     chosen = times[np.arange(times.shape[0]), idx].sum()
     return float(chosen / times.min(axis=1).sum() - 1.0)
@@ -79,6 +106,10 @@ def regret(times: np.ndarray, y_pred: np.ndarray, grid=GRID) -> float:
 def default_regret(times: np.ndarray, grid=GRID) -> float:
     j0 = list(grid).index(0)
     return float(times[:, j0].sum() / times.min(axis=1).sum() - 1.0)
+
+
+def _finite_cols(times: np.ndarray) -> np.ndarray:
+    return np.isfinite(times).all(axis=0)
 
 
 def init_params(feats: np.ndarray, seed: int = 0) -> np.ndarray:
@@ -153,7 +184,8 @@ def build_and_train(mode: str, out_dir: str = WEIGHTS_DIR, epochs: int = 600, lo
         labels_all.append(lab)
         meta_sets.append({"set": name, "groups": int(feats.shape[0]), "default_delta": default,
                           "default_regret": default_regret(times),
-                          "label_hist": {str(j): int((lab == j).sum()) for j in GRID}})
+                          "swept": [j for j, ok in zip(GRID, _finite_cols(times)) if ok],
+                          "label_hist": {str(j): int((lab == j).sum()) for j in GRID if (lab == j).any()}})
         log(json.dumps(meta_sets[-1]))
     F = np.concatenate(feats_all)
     Y = np.concatenate(labels_all)
@@ -164,30 +196,35 @@ def build_and_train(mode: str, out_dir: str = WEIGHTS_DIR, epochs: int = 600, lo
             "features": "log2(1 + raw): h(s,t), deg(s), deg(t), w mean/std/min/max, n, m, |V_q|, |E_q|, "
                         "mean query-graph degree",
             "train_mae": float(np.abs(pred - Y).mean())}
+    meta["eval"] = evaluate(mode, log=log, model=model)
     path = save(model, mode, meta, out_dir)
     log(json.dumps({"saved": path, "train_loss": loss, "train_mae": meta["train_mae"]}))
     model.close()
     return meta
 
 
-def evaluate(mode: str, log=print) -> dict:
-    """Regret of the saved model on the held-out road-like benchmark queries
-    (the 1,000 near/mid/far pairs; training used other seeds)."""
+def evaluate(mode: str, log=print, model=None) -> dict:
+    """Regret of the model (default: the saved one) on the held-out road-like
+    benchmark queries (the 1,000 near/mid/far pairs; training used other seeds)."""
     from workloads import config_workload
 
     wl = config_workload(2)
     g, pairs = wl["graph"], wl["batches"]["nmf"]
-    model = load_model(mode)
+    own = model is None
+    if own:
+        model = load_model(mode)
     if model is None:
         raise FileNotFoundError(weights_path(mode))
     with ppsp.Graph.from_csr(g) as G:
         feats, times, default = sweep(G, pairs, mode)
     y = model.predict(feats)
+    lab = labels_from_times(times)
     res = {"mode": mode, "eval_set": "road1024 near/mid/far (bench queries)", "groups": int(feats.shape[0]),
            "regret_learned": regret(times, y), "regret_default": default_regret(times),
-           "best_grid_hist": {str(j): int((labels_from_times(times) == j).sum()) for j in GRID},
+           "best_grid_hist": {str(j): int((lab == j).sum()) for j in GRID if (lab == j).any()},
            "pred_mean": float(y.mean())}
-    model.close()
+    if own:
+        model.close()
     log(json.dumps(res))
     return res
 
