@@ -189,6 +189,7 @@ struct Smem {
     u32 lfar_n[2];
     u32 lfar_fb, lfar_tgt, lspill, tov;
     u32 lrecov, lidle;  // spill recovered since the last processed bucket; decisions without one
+    u32 lfar_after;     // far-list entries right after the last re-bucketing
     // step scalars
     u64 minkey_in, minkey_acc;
     u32 count, overflow, dir0, dir1, tile, flag, total, nitems, cert;
@@ -562,8 +563,8 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
 // its current distance when nothing else is left.
 template <typename D>
 struct LR {
-    static constexpr u32 NB = 16;                          // buckets in the ring
-    static constexpr u32 CAP = sizeof(D) == 4 ? 512 : 256;  // entries per bucket
+    static constexpr u32 NB = 32;                          // buckets in the ring
+    static constexpr u32 CAP = sizeof(D) == 4 ? 256 : 128;  // shared-memory entries per bucket
     static constexpr size_t bytes() { return (size_t)NB * CAP * (4 + sizeof(D)) + NB * 4; }
 };
 
@@ -778,6 +779,7 @@ __device__ void redistribute_far(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, c
         sm.lfar_fb = nb;
         sm.lfar_n[fb] = 0;
         sm.lfar_min[fb] = INF64;
+        sm.lfar_after = sm.lfar_n[nb];
     }
     __syncthreads();
 }
@@ -831,6 +833,7 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
         sm.llate = INF64;
         sm.lrecov = 0;
         sm.lidle = 0;
+        sm.lfar_after = 0;
         sm.cnt_dir[0] = sm.cnt_dir[1] = 0;
     }
     __syncthreads();
@@ -874,7 +877,10 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
                 // between two processed buckets (re-spilled entries wait for
                 // the bucket in front of them to be processed first)
                 sm.flag = 2;
-            } else if (fm != INF64 && (fm <= rb || fm < cur + LR<D>::NB / 2)) {
+            } else if (fm != INF64 && (fm <= rb || fm < cur + LR<D>::NB / 2 ||
+                                       (sm.lfar_n[fb] > c.slot.qcap / 2 && sm.lfar_n[fb] > 2 * sm.lfar_after))) {
+                // far entries due soon, an empty ring, or a far list filling up
+                // with stale entries (re-bucketing drops them)
                 if (fm <= rb && fm > cur + 1) sm.lcur = fm - 1;
                 sm.flag = 1;
             } else if (rb != INF64) {

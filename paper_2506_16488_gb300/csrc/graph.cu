@@ -163,7 +163,7 @@ ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u
     const u64 W = dist_bits / 8;
     const u64 words = (flat_cap + 31) / 32;
     auto al = [](u64 x) { return (x + 255) & ~255ull; };
-    const u64 ocap = std::max<u64>(16 * 256, flat_cap / 4) / 16 * 16;
+    const u64 ocap = std::max<u64>(32 * 256, flat_cap / 4) / 32 * 32;
     const u64 b_dist = al(flat_cap * W), b_bm = al(words * 4), b_q = al((u64)qcap * 4),
               b_fd = al((u64)qcap * W), b_t = al((u64)tcap * 4), b_st = al(sizeof(SlotState)),
               b_of = al(ocap * 4), b_od = al(ocap * W);

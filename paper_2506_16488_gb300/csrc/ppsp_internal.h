@@ -99,7 +99,7 @@ struct SlotDev {
     void* fd[2];          // one-CTA teams: distance stored with each far-list entry
     u32* of;              // one-CTA teams: bucket overflow (flat index), ocap entries
     void* od;             //   and the stored distances
-    u32 ocap;             //   ocap / 16 entries per ring bucket
+    u32 ocap;             //   split evenly between the ring's buckets
     u32* touched;         // flat indices that left infinity, tcap entries
     SlotState* st;
     u64 flat_cap;         // k_cap * n

@@ -81,6 +81,8 @@ def sweep(G: ppsp.Graph, pairs: np.ndarray, mode: str, grid=GRID, stream=None, r
                 best_total, worse = tot, 0
             else:
                 worse += 1
+                if tot > 5 * best_total:  # far past the optimum: stop walking this way
+                    break
             k += direction
     ng = state["feats"].shape[0]
     times = np.full((ng, len(grid)), np.inf)

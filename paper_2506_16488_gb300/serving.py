@@ -234,7 +234,9 @@ def slot_bytes(n: int, searches_per_slot: int, dist_bits: int) -> int:
     flat = (flat + 63) // 64 * 64
     qcap = min(flat, flat // 8 + 4096)
     tcap = min(flat, flat // 4 + 4096)
-    return flat * dist_bits // 8 + 2 * (flat // 8) + 2 * 4 * qcap + 2 * (dist_bits // 8) * qcap + 4 * tcap
+    ocap = max(32 * 256, flat // 4) // 32 * 32
+    return (flat * dist_bits // 8 + 2 * (flat // 8) + 2 * 4 * qcap + 2 * (dist_bits // 8) * qcap + 4 * tcap
+            + ocap * (4 + dist_bits // 8))
 
 
 def memory_model(n: int, lane_ctas: int, dist_bits: int) -> Callable[[np.ndarray], int]:
