@@ -739,16 +739,86 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
     const u32 excl = block_excl_scan<B>(deg, sm, &total);
     sm.pre[t] = (t < cnt) ? excl : total;
     __syncthreads();
-    for (u32 e = t; e < total; e += B) {
-        u32 lo = 0, hi = cnt;
-        while (hi - lo > 1) {
-            const u32 mid = (lo + hi) >> 1;
-            if (sm.pre[mid] <= e) lo = mid; else hi = mid;
+    if (c.pair) {
+        // pair groups: RX edges per thread at a time, their loads and atomics
+        // issued together (instruction-level parallelism on the dependent
+        // edge -> distance -> atomicMin chain)
+        constexpr int RX = 4;
+        for (u32 e0 = t; e0 < total; e0 += RX * B) {
+            u32 v2[RX], si[RX], f2[RX];
+            u64 nd[RX], own[RX], oth[RX], old[RX];
+            int2 pv2[RX];
+            bool ok[RX];
+#pragma unroll
+            for (int k = 0; k < RX; ++k) {
+                const u32 e = e0 + k * B;
+                ok[k] = e < total;
+                v2[k] = 0;
+                nd[k] = DT<D>::INF;
+                si[k] = 0;
+                if (ok[k]) {
+                    u32 lo = 0, hi = cnt;
+                    while (hi - lo > 1) {
+                        const u32 mid = (lo + hi) >> 1;
+                        if (sm.pre[mid] <= e) lo = mid; else hi = mid;
+                    }
+                    const uint2 ew = __ldg(a.g.edges + sm.beg[lo] + (e - sm.pre[lo]));
+                    v2[k] = ew.x;
+                    si[k] = sm.si[lo];
+                    nd[k] = sm.d[lo] + (u64)ew.y;
+                    ++c.c_e;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RX; ++k) {
+                pv2[k] = make_int2(0, 0);
+                if (ok[k]) {
+                    if (sm.pot_any) pv2[k] = __ldg(a.g.pc + v2[k]);
+                    u64 x0, x1;
+                    ld_pair(c.dist, v2[k], x0, x1);
+                    own[k] = si[k] ? x1 : x0;
+                    oth[k] = si[k] ? x0 : x1;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RX; ++k) {
+                old[k] = 0;
+                if (ok[k]) {
+                    if (nd[k] > DT<D>::MAXV) {
+                        atomicOr(a.err, ERRB_OVERFLOW);
+                        ok[k] = false;
+                    } else if (nd[k] < own[k]) {
+                        f2[k] = (v2[k] << 1) | si[k];
+                        old[k] = amin_dist(c.dist + f2[k], nd[k]);
+                    } else {
+                        ok[k] = false;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RX; ++k) {
+                if (!ok[k] || nd[k] >= old[k]) continue;
+                ++c.c_r;
+                if (old[k] == DT<D>::INF) touch_local<D, B>(c, sm, f2[k]);
+                if (oth[k] != DT<D>::INF) try_mu(a, c.G, sm, c.G.qbeg, nd[k] + oth[k]);
+                i64 key, pv;
+                key_pv<B>(a, c.G, sm, si[k], pv2[k], nd[k], key, pv);
+                if (pruned(pv, sm.bound[si[k]])) continue;
+                insert_local<D, B>(c, sm, L, f2[k], si[k], key, nd[k]);
+            }
         }
-        const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
-        const uint2 ew = __ldg(a.g.edges + edge);
-        ++c.c_e;
-        relax_local<D, B>(a, c, sm, L, sm.si[lo], sm.d[lo], ew);
+    } else {
+        for (u32 e = t; e < total; e += B) {
+            u32 lo = 0, hi = cnt;
+            while (hi - lo > 1) {
+                const u32 mid = (lo + hi) >> 1;
+                if (sm.pre[mid] <= e) lo = mid; else hi = mid;
+            }
+            const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
+            const uint2 ew = __ldg(a.g.edges + edge);
+            ++c.c_e;
+            relax_local<D, B>(a, c, sm, L, sm.si[lo], sm.d[lo], ew);
+        }
     }
     __syncthreads();
 }
@@ -1371,8 +1441,15 @@ constexpr size_t engine_smem_bytes() {
     return ((sizeof(Smem<B>) + 15) & ~(size_t)15) + LR<D>::bytes();
 }
 
+// Threads per SM the engine is compiled to keep resident (register budget):
+// 1024 keeps two 512-thread CTAs per SM at 64 registers per thread.
+#ifndef PPSP_ENGINE_SM_THREADS
+#define PPSP_ENGINE_SM_THREADS 1024
+#endif
+
 template <typename D, int B>
-__global__ void __launch_bounds__(B) engine_kernel(EngineArgs a) {
+__global__ void __launch_bounds__(B, (PPSP_ENGINE_SM_THREADS / B) > 0 ? (PPSP_ENGINE_SM_THREADS / B) : 1)
+    engine_kernel(EngineArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<B>& sm = *reinterpret_cast<Smem<B>*>(smem_raw);
     TeamCtx tc;
