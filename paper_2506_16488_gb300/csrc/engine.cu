@@ -1442,9 +1442,10 @@ constexpr size_t engine_smem_bytes() {
 }
 
 // Threads per SM the engine is compiled to keep resident (register budget):
-// 1024 keeps two 512-thread CTAs per SM at 64 registers per thread.
+// 512 gives one 512-thread CTA per SM up to 128 registers per thread (the
+// four-way relaxation keeps its loads in registers instead of spilling).
 #ifndef PPSP_ENGINE_SM_THREADS
-#define PPSP_ENGINE_SM_THREADS 1024
+#define PPSP_ENGINE_SM_THREADS 512
 #endif
 
 template <typename D, int B>
