@@ -354,6 +354,30 @@ def run_ours(args):
         best["tried"] = [{"team_ctas": r["team_ctas"], "value": r["value"]} for r in runs]
         return best
 
+    # other batch strategies on the same batch (Sec. 4.2 Plain*, Sec. 4.3
+    # Plain-SSSP and VC-SSSP), one timed run each after one untimed run
+    compare = {}
+    for strat in args.compare:
+        copts = dict(mode=mode, strategy=strat, stream=stream.cuda_stream, max_ctas=args.max_ctas)
+        if args.delta:
+            copts["delta"] = args.delta
+        cp = G.plan(pairs, **copts)
+        co = torch.zeros(k, dtype=torch.int64, device="cuda")
+        cp.run(co.data_ptr())
+        cp.sync()
+        with torch.cuda.stream(stream):
+            flush.fill_(7)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cp.run(co.data_ptr())
+        e1.record(stream)
+        cc = cp.sync()
+        ms = e0.elapsed_time(e1)
+        assert np.array_equal(co.cpu().numpy().view(np.uint64), got), strat
+        cp.close()
+        compare[strat] = {"value": k / (ms / 1000.0), "unit": "queries/s", "ms": ms,
+                          "searches": cc["searches"], "edges": cc["edges"]}
+
     plain = best_plain(delta=args.delta or default_delta)
     plain["delta"] = f"default {default_delta}" if not args.delta else f"fixed {args.delta}"
     plain_same = best_plain(**({"delta": args.delta} if args.delta else {}))
@@ -392,6 +416,7 @@ def run_ours(args):
         "plain_same_delta": plain_same,
         "speedup_vs_plain": qps / world / plain["value"],
         "speedup_vs_plain_same_delta": qps / world / plain_same["value"],
+        **({"strategies": compare} if compare else {}),
         "counters": cnt,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
@@ -483,6 +508,8 @@ def main():
     ap.add_argument("--plain-teams", type=int, nargs="*", default=[16, 64, 0],
                     help="team sizes tried for the plain one-query-at-a-time baseline (0 = all CTAs)")
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on resident CTAs (profiling)")
+    ap.add_argument("--compare", nargs="*", default=[], choices=["plain_star", "sssp", "vc", "auto"],
+                    help="also time these batch strategies on the same batch (one run each)")
     ap.add_argument("--rates", type=float, nargs="*", default=[1000, 5000, 20000, 50000],
                     help="serving (config 5): offered query rates")
     ap.add_argument("--duration", type=float, default=2.0, help="serving (config 5): seconds per rate")

@@ -62,17 +62,38 @@ enum {
 /* Graph flags. */
 enum { PPSP_UNDIRECTED = 1u };
 
-/* Frontier representation policy (App. B "Sparse-Dense Optimization"). */
+/* Frontier representation policy (App. B "Sparse-Dense Optimization").
+ * AUTO: a group run by one CTA keeps its frontier as Delta*-stepping buckets
+ * in shared memory (overflow and far-ahead entries in the slot); a group run
+ * by several CTAs uses a queue while the frontier is small and a bitmap once
+ * it exceeds (searches * n) / dense_den entries.  SPARSE / DENSE force the
+ * queue / bitmap for every group. */
 enum { PPSP_FRONTIER_AUTO = 0, PPSP_FRONTIER_SPARSE = 1, PPSP_FRONTIER_DENSE = 2 };
 
 /* Layout of the per-search tentative-distance arrays of one batch group. */
 enum { PPSP_LAYOUT_AUTO = 0, PPSP_LAYOUT_INTERLEAVED = 1, PPSP_LAYOUT_STACKED = 2 };
 
-/* How a batch is executed (Sec. 4.2 and the batch baselines of Sec. 6). */
+/* How a batch is executed (Sec. 4.2, Sec. 4.3 and the batch baselines of Sec. 6). */
 enum {
     PPSP_BATCH_MULTI = 0,      /* Multi-BiDS: one search per query-graph vertex, shared  */
     PPSP_BATCH_PLAIN_STAR = 1, /* Plain*: every query its own pair of searches, all at once */
-    PPSP_BATCH_PLAIN = 2       /* Plain: one query at a time, each on the whole GPU       */
+    PPSP_BATCH_PLAIN = 2,      /* Plain: one query at a time, each on the whole GPU       */
+    PPSP_BATCH_SSSP = 3,       /* Plain-SSSP (Sec. 4.3): a single-source search from every
+                                  query source; answers read from its distances          */
+    PPSP_BATCH_VC = 4,         /* VC-SSSP (Sec. 4.3): single-source searches only from a
+                                  vertex cover of G_q (exact up to 32 vertices per
+                                  component, greedy above); undirected graphs.  For both
+                                  SSSP strategies a search stops once every one of its
+                                  targets is settled (no remaining key below the largest
+                                  target distance, the multi-target form of ET's prune) */
+    PPSP_BATCH_AUTO = 5        /* per connected component of G_q: an isolated pair runs as
+                                  a pair; with BiD-A* potentials a star runs as one SSSP
+                                  search from its centre and any other component as
+                                  independent pairs (Plain*); without potentials a
+                                  component with a vertex cover of at most a quarter of
+                                  its vertices runs as VC-SSSP, any other as Multi-BiDS.
+                                  ET / A*: sources with 4 or more targets run one
+                                  multi-target search                                   */
 };
 
 /*
@@ -263,6 +284,22 @@ ppsp_status ppsp_plan_group_times(ppsp_plan* p, uint64_t* out_ns, uint64_t cap, 
 
 /* 1 if the plan's last run replayed a captured CUDA graph, else 0. */
 ppsp_status ppsp_plan_uses_graph(const ppsp_plan* p, int32_t* out);
+
+/* Source selection of the SSSP-based batch strategies (Sec. 4.3), host only
+ * (no device work, usable without a GPU).
+ *   pairs      host array of k (s, t) vertex-id pairs (uint32, row-major k x 2)
+ *   strategy   PPSP_BATCH_SSSP (the source of each query) or PPSP_BATCH_VC
+ *              (an endpoint in a vertex cover of the query graph: minimum by
+ *              exhaustive branch and bound for components of at most 32
+ *              vertices, greedy by uncovered degree above)
+ *   src_out    host array of k: the vertex whose single-source search answers
+ *              pair q, 0xFFFFFFFF for s == t (no search); caller-owned
+ *   n_sources  number of distinct sources, i.e. full searches the plan runs
+ * This is exactly the selection ppsp_plan_create makes for these strategies.
+ * Vertex ids are not range-checked (no graph). Errors: PPSP_ERR_INVALID_ARG for
+ * null pointers or another strategy. */
+ppsp_status ppsp_batch_sources(const uint32_t* pairs, uint64_t k, int32_t strategy, uint32_t* src_out,
+                               uint64_t* n_sources);
 
 /*
  * Learned stepping increment.  The paper tunes Delta of Delta*-stepping by

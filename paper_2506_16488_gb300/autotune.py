@@ -1,7 +1,9 @@
 """Autotuner for the launch configuration of a batch.
 
 The knobs change only speed, never answers (Theorems 3.3/3.4 hold for any
-schedule): threads per CTA, CTAs per pair team, CTAs per multi-search team,
+schedule): the batch strategy (Multi-BiDS, the per-component AUTO choice,
+Plain*, VC-SSSP: the per-batch choice of Sec. 4.3), threads per CTA, CTAs per
+pair team, CTAs per multi-search team,
 the sparse/dense frontier threshold (App. B), the distance layout of
 multi-search groups, and the frontier policy.  The tuner runs the batch's plan
 with one knob changed at a time (coordinate descent from the library's
@@ -25,6 +27,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "tuning", "cache.json")
 
 SPACE = (
+    ("strategy", ("auto", "plain_star", "vc")),
     ("block_threads", (512, 256, 1024)),
     ("team_ctas", (0, 1, 2, 4, 8)),
     ("big_team_ctas", (0, 8, 16, 32, 64, 128)),
@@ -73,6 +76,7 @@ def tune(G: ppsp.Graph, pairs: np.ndarray, mode: str, base: dict | None = None, 
     out = torch.zeros(pairs.shape[0], dtype=torch.int64, device="cuda")
     best = dict(base or {})
     best.setdefault("mode", mode)
+    best.setdefault("strategy", "multi")
     t_best, ref = _time_plan(G, pairs, best, reps, stream, out)
     trials = [{"opts": dict(best), "ms": t_best}]
     t0 = time.time()

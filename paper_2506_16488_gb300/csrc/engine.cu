@@ -86,7 +86,14 @@ __device__ __forceinline__ u64 global_ns() {
 // correction.  Below 2^48 the float32 estimate is within 1 of the result
 // (relative error about 2^-24 on a value below 2^24); above, float64.
 __device__ __forceinline__ u64 isqrt_u64(u64 x) {
-    u64 r = (x < (1ull << 48)) ? (u64)sqrtf((float)x) : (u64)sqrt((double)x);
+    if (x < (1ull << 48)) {
+        // result below 2^24: 32-bit candidate, 32 x 32 -> 64-bit checks
+        u32 r = (u32)sqrtf((float)x);
+        while ((u64)r * r > x) --r;
+        while ((u64)(r + 1) * (r + 1) <= x) ++r;
+        return r;
+    }
+    u64 r = (u64)sqrt((double)x);
     while (r * r > x) --r;
     while ((r + 1) * (r + 1) <= x) ++r;
     return r;
@@ -196,7 +203,37 @@ struct Smem {
     u32 cnt_dir[2];
     u32 group;
     u64 mu0;
+#ifdef PPSP_PHASE_CLOCKS
+    u64 ph_t, ph_acc[16];  // thread 0's clock at the last mark; cycles per phase
+#endif
 };
+
+// Opt-in profiling of the one-CTA path (-DPPSP_PHASE_CLOCKS): thread 0 adds
+// the SM cycles since its previous mark to phase k; the totals of all CTAs
+// are summed in g_phase_clk and read with ppsp_debug_phase_clocks.  Off in
+// normal builds (the macros expand to nothing).
+#ifdef PPSP_PHASE_CLOCKS
+__device__ unsigned long long g_phase_clk[16];
+#define PH_START(sm)                                    \
+    do {                                                \
+        if (threadIdx.x == 0) (sm).ph_t = clock64();    \
+    } while (0)
+#define PH_MARK(sm, k)                                  \
+    do {                                                \
+        if (threadIdx.x == 0) {                         \
+            const u64 now_ = clock64();                 \
+            (sm).ph_acc[k] += now_ - (sm).ph_t;         \
+            (sm).ph_t = now_;                           \
+        }                                               \
+    } while (0)
+#else
+#define PH_START(sm) \
+    do {             \
+    } while (0)
+#define PH_MARK(sm, k) \
+    do {               \
+    } while (0)
+#endif
 
 template <int B>
 __device__ __forceinline__ u32 block_excl_scan(u32 x, Smem<B>& sm, u32* total) {
@@ -243,6 +280,9 @@ struct GCtx {
     u32 n;
     // per-thread counters
     u64 c_x, c_e, c_r, c_p, c_t;
+    // one-CTA path: this thread's net change of the per-direction entry
+    // counts, added to the shared counts once per tile (flush_dir)
+    int dc0, dc1;
 };
 
 __device__ __forceinline__ u32 flat_of(const GroupDev& G, u32 n, u32 v, u32 i) {
@@ -306,16 +346,21 @@ __device__ __forceinline__ PartnerDev partner(const EngineArgs& a, const Smem<B>
 template <int B>
 __device__ __forceinline__ void try_mu(const EngineArgs& a, const GroupDev& G, Smem<B>& sm,
                                        u32 qe, u64 s) {
+    if (G.qcnt <= 1 || G.mode != GM_BIDIR) {
+        // one query edge: the prune bound of every search is mu itself.  The
+        // shared-memory mirror is never below mu (exact for one-CTA teams,
+        // refreshed from mu every tile otherwise), so s >= mirror cannot
+        // improve mu; otherwise lower the mirror and write mu without
+        // waiting for the old value (s is the length of a real s-t path).
+        if (s >= sm.bound[0]) return;
+        atomicMin(reinterpret_cast<unsigned long long*>(&sm.bound[0]), (unsigned long long)s);
+        if (G.scnt == 2) atomicMin(reinterpret_cast<unsigned long long*>(&sm.bound[1]), (unsigned long long)s);
+        atomicMin(reinterpret_cast<unsigned long long*>(a.mu + qe), (unsigned long long)s);
+        return;
+    }
     if (s >= ldcg64(a.mu + qe)) return;
     u64 old = amin64(a.mu + qe, s);
     if (s >= old) return;
-    if (G.qcnt <= 1 || G.mode != GM_BIDIR) {
-        // one query edge: the prune bound of every search is mu itself
-        // (shared-memory mirror, read by one-CTA teams)
-        atomicMin(reinterpret_cast<unsigned long long*>(&sm.bound[0]), (unsigned long long)s);
-        if (G.scnt == 2) atomicMin(reinterpret_cast<unsigned long long*>(&sm.bound[1]), (unsigned long long)s);
-        return;
-    }
     QEdgeDev e = a.qedges[qe];
     u32 ends[2] = {e.a, e.b};
 #pragma unroll
@@ -482,7 +527,7 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
         if (c.G.mode == GM_BIDIR)
             b = (c.G.qcnt == 1) ? ldcg64(a.mu + c.G.qbeg) : ldcg64(a.mumax + c.G.sbeg + t);
         else if (c.G.mode == GM_SSSP)
-            b = INF64;
+            b = sm.bound[t];  // set from the round's target snapshot
         else
             b = ldcg64(a.mu + c.G.qbeg);
         sm.bound[t] = b;
@@ -589,7 +634,12 @@ template <typename D, int B>
 __device__ __forceinline__ void insert_local(GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L, u32 f, u32 i,
                                              i64 key, u64 d) {
     const u64 step = sm.lstep;
-    u64 b = ((u64)key + step - 1) / step;
+    // b = ceil(key / step), in 32 bits when both fit (the common case)
+    u64 b;
+    if ((((u64)key | step) >> 32) == 0)
+        b = key == 0 ? 0 : (u64)(((u32)key - 1u) / (u32)step + 1u);
+    else
+        b = ((u64)key + step - 1) / step;
     const u64 cur = sm.lcur;
     if (b <= cur) {
         // already under the threshold: due at the next step; remember the key
@@ -600,7 +650,11 @@ __device__ __forceinline__ void insert_local(GCtx<D>& c, Smem<B>& sm, const Loca
     bool stored = false;
     if (b < cur + LR<D>::NB) {
         const u32 s = (u32)(b % LR<D>::NB);
-        const u32 pos = atomicAdd(&L.rn[s], 1u);
+        // one shared-memory atomic per bucket per warp
+        cg::coalesced_group peers = cg::labeled_partition(cg::coalesced_threads(), (int)s);
+        u32 pos = 0;
+        if (peers.thread_rank() == 0) pos = atomicAdd(&L.rn[s], (u32)peers.size());
+        pos = peers.shfl(pos, 0) + peers.thread_rank();
         if (pos < LR<D>::CAP) {
             L.rf[s * LR<D>::CAP + pos] = f;
             L.rd[s * LR<D>::CAP + pos] = (D)d;
@@ -616,7 +670,7 @@ __device__ __forceinline__ void insert_local(GCtx<D>& c, Smem<B>& sm, const Loca
         }
     } else {
         const u32 fb = sm.lfar_tgt;
-        const u32 pos = atomicAdd(&sm.lfar_n[fb], 1u);
+        const u32 pos = agg_inc(&sm.lfar_n[fb]);
         if (pos < c.slot.qcap) {
             c.slot.q[fb][pos] = f;
             reinterpret_cast<D*>(c.slot.fd[fb])[pos] = (D)d;
@@ -630,13 +684,28 @@ __device__ __forceinline__ void insert_local(GCtx<D>& c, Smem<B>& sm, const Loca
         sm.lspill = 1;
     }
     ++c.c_p;
-    if (c.G.scnt == 2) atomicAdd(&sm.cnt_dir[i], 1u);
+    if (i) ++c.dc1; else ++c.dc0;
+}
+
+// Add the warp's net per-direction entry counts to the shared counts (all
+// threads of the CTA call this, converged, before a barrier).
+template <typename D, int B>
+__device__ __forceinline__ void flush_dir(GCtx<D>& c, Smem<B>& sm) {
+    if (c.G.scnt == 2) {
+        const u32 s0 = __reduce_add_sync(0xffffffffu, (u32)c.dc0);
+        const u32 s1 = __reduce_add_sync(0xffffffffu, (u32)c.dc1);
+        if ((threadIdx.x & 31) == 0) {
+            if (s0) atomicAdd(&sm.cnt_dir[0], s0);
+            if (s1) atomicAdd(&sm.cnt_dir[1], s1);
+        }
+    }
+    c.dc0 = c.dc1 = 0;
 }
 
 template <typename D, int B>
 __device__ __forceinline__ void touch_local(GCtx<D>& c, Smem<B>& sm, u32 f) {
     ++c.c_t;
-    const u32 pos = atomicAdd(&sm.tn, 1u);
+    const u32 pos = agg_inc(&sm.tn);
     if (pos < c.slot.tcap)
         c.slot.touched[pos] = f;
     else
@@ -684,6 +753,31 @@ __device__ __forceinline__ void relax_local(const EngineArgs& a, GCtx<D>& c, Sme
     insert_local<D, B>(c, sm, L, f2, i, key, nd);
 }
 
+// SSSP-based groups (Sec. 4.3): the largest tentative distance of the
+// group's targets, or INF while one of them is unreached.  Called by one full
+// warp.  Every entry that remains with a key at least this large cannot lower
+// any target, so it is both the prune bound and the stop certificate of the
+// search (the multi-target form of ET, Sec. 3.2).
+template <typename D, int B>
+__device__ __forceinline__ u64 sssp_target_max(const EngineArgs& a, const GCtx<D>& c, const Smem<B>& sm) {
+    const u32 lane = threadIdx.x & 31u;
+    u64 m = 0;
+    bool all = true;
+    for (u32 q = lane; q < c.G.qcnt; q += 32) {
+        const u32 tv = sm.pcached ? sm.pcache[q].j : a.qedges[c.G.qbeg + q].b;
+        const u64 d = ld_dist(c.dist + flat_of(c.G, c.n, tv, 0));
+        all = all && d != DT<D>::INF;
+        m = d > m ? d : m;
+    }
+    all = __all_sync(0xffffffffu, all);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 y = __shfl_xor_sync(0xffffffffu, m, o);
+        m = y > m ? y : m;
+    }
+    return (all && c.G.qcnt > 0) ? m : INF64;
+}
+
 // mode 0: entries of the current bucket (extract); mode 1: far-list or spill
 // entries (re-bucket, nothing is expanded).  src_f / src_d hold the tile.
 template <typename D, int B>
@@ -709,7 +803,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
         } else {
             d = ld_dist(c.dist + f);
         }
-        if (c.G.scnt == 2) atomicSub(&sm.cnt_dir[i], 1u);  // the stored entry is consumed
+        if (i) --c.dc1; else --c.dc0;  // the stored entry is consumed
         if (d != DT<D>::INF && (dins == DT<D>::INF || d == dins)) {
             i64 key, pv;
             key_pv<B>(a, c.G, sm, i, pv2, d, key, pv);
@@ -732,13 +826,16 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
         }
     }
     if (mode == 1) {
+        flush_dir<D, B>(c, sm);
         __syncthreads();
         return;
     }
+    PH_MARK(sm, 1);  // staging + extraction of thread 0's entry
     u32 total;
     const u32 excl = block_excl_scan<B>(deg, sm, &total);
     sm.pre[t] = (t < cnt) ? excl : total;
     __syncthreads();
+    PH_MARK(sm, 2);  // scan, including the wait for the slowest extraction
     if (c.pair) {
         // pair groups: RX edges per thread at a time, their loads and atomics
         // issued together (instruction-level parallelism on the dependent
@@ -769,6 +866,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
                     ++c.c_e;
                 }
             }
+            PH_MARK(sm, 7);  // edge search + edge loads issued
 #pragma unroll
             for (int k = 0; k < RX; ++k) {
                 pv2[k] = make_int2(0, 0);
@@ -780,6 +878,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
                     oth[k] = si[k] ? x0 : x1;
                 }
             }
+            PH_MARK(sm, 8);  // edge loads returned, distance loads issued
 #pragma unroll
             for (int k = 0; k < RX; ++k) {
                 old[k] = 0;
@@ -788,13 +887,19 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
                         atomicOr(a.err, ERRB_OVERFLOW);
                         ok[k] = false;
                     } else if (nd[k] < own[k]) {
+                        // WriteMin without waiting for the old value: the
+                        // distance just read decides success (a concurrent
+                        // smaller write only makes this entry stale, and
+                        // extraction drops stale entries)
                         f2[k] = (v2[k] << 1) | si[k];
-                        old[k] = amin_dist(c.dist + f2[k], nd[k]);
+                        amin_dist(c.dist + f2[k], nd[k]);
+                        old[k] = own[k];
                     } else {
                         ok[k] = false;
                     }
                 }
             }
+            PH_MARK(sm, 9);  // distances returned, atomics issued
 #pragma unroll
             for (int k = 0; k < RX; ++k) {
                 if (!ok[k] || nd[k] >= old[k]) continue;
@@ -806,6 +911,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
                 if (pruned(pv, sm.bound[si[k]])) continue;
                 insert_local<D, B>(c, sm, L, f2[k], si[k], key, nd[k]);
             }
+            PH_MARK(sm, 10);  // atomics returned, potentials, mu, insertions
         }
     } else {
         for (u32 e = t; e < total; e += B) {
@@ -820,7 +926,10 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
             relax_local<D, B>(a, c, sm, L, sm.si[lo], sm.d[lo], ew);
         }
     }
+    PH_MARK(sm, 3);  // thread 0's relaxations
+    flush_dir<D, B>(c, sm);
     __syncthreads();
+    PH_MARK(sm, 4);  // wait for the slowest relaxation
 }
 
 // Re-bucket every entry of the far list `fb` (relative to the current bucket);
@@ -908,21 +1017,33 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
     }
     __syncthreads();
     // Init: the sources (key 0) go to the first step
+    c.dc0 = c.dc1 = 0;
     if (t < G.scnt) insert_local<D, B>(c, sm, L, flat_of(G, c.n, sm.src[t], t), t, 0, 0);
+    flush_dir<D, B>(c, sm);
+#ifdef PPSP_PHASE_CLOCKS
+    if (t < 16) sm.ph_acc[t] = 0;
+#endif
     __syncthreads();
+    PH_START(sm);
     u64 rounds = 0;
     for (;;) {
-        // choose the next bucket (thread 0), moving far entries into the window
-        // when they are due soon or the ring is empty
+        // choose the next bucket (warp 0 finds the first non-empty bucket of
+        // the ring, thread 0 decides), moving far entries into the window when
+        // they are due soon or the ring is empty
+        u64 rb = INF64;
+        if (G.mode == GM_SSSP && t >= 32 && t < 64) {
+            const u64 m = sssp_target_max<D, B>(a, c, sm);
+            if (t == 32 && m < sm.bound[0]) sm.bound[0] = m;  // only thread 32 writes it here
+        }
+        if (t < 32) {
+            const u64 cur = sm.lcur;
+            const bool full = t >= 1 && t < LR<D>::NB && L.rn[(u32)((cur + t) % LR<D>::NB)] != 0;
+            const u32 mask = __ballot_sync(0xffffffffu, full);
+            if (mask) rb = cur + (u32)(__ffs(mask) - 1);
+        }
         if (t == 0) {
             sm.flag = 0;  // 0 = process lcur, 1 = redistribute, 2 = recover, 3 = done
             const u64 cur = sm.lcur;
-            u64 rb = INF64;
-            for (u32 j = 1; j < LR<D>::NB; ++j)
-                if (L.rn[(u32)((cur + j) % LR<D>::NB)] != 0) {
-                    rb = cur + j;
-                    break;
-                }
             const u32 fb = sm.lfar_fb;
             const u64 fm = sm.lfar_n[fb] ? sm.lfar_min[fb] : INF64;
             bool stop = false;
@@ -933,7 +1054,7 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
             // and a prune value >= its key; once that reaches the largest prune
             // bound of the group, every remaining entry would be pruned.
             const u64 nextb = rb < fm ? rb : fm;
-            if (!stop && !sm.lspill && nextb != INF64 && G.mode != GM_SSSP) {
+            if (!stop && !sm.lspill && nextb != INF64) {
                 u64 bmax = 0;
                 for (u32 i = 0; i < G.scnt; ++i) bmax = sm.bound[i] > bmax ? sm.bound[i] : bmax;
                 u64 lb = (nextb - 1) * sm.lstep + 1;  // keys in buckets >= nextb
@@ -971,24 +1092,29 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
                 sm.flag = 3;
             }
             if (sm.flag == 2) sm.lrecov = 1;
-            if (sm.flag == 0) sm.lrecov = 0;
+            if (sm.flag == 0) {
+                sm.lrecov = 0;
+                sm.llate = INF64;  // late entries of this bucket's processing
+            }
         }
         __syncthreads();
+        // every path below passes a barrier before thread 0 writes the flag
+        // again (a chosen bucket is never empty)
         const u32 what = sm.flag;
-        __syncthreads();
+        PH_MARK(sm, 0);  // decision
         if (what == 3) break;
         if (what == 1) {
             redistribute_far<D, B>(a, c, sm, L);
+            PH_MARK(sm, 5);
             continue;
         }
         if (what == 2) {
             recover_spill<D, B>(a, c, sm, L, nwords);
+            PH_MARK(sm, 6);
             continue;
         }
         // process bucket lcur: theta = lcur * step
         ++rounds;
-        if (t == 0) sm.llate = INF64;
-        __syncthreads();
         const u32 s = (u32)(sm.lcur % LR<D>::NB);
         const u32 ob = c.slot.ocap / LR<D>::NB;
         const u32 n = min(L.rn[s], LR<D>::CAP + ob);
@@ -1004,12 +1130,18 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
                     sm.d[t] = (u64)__ldcg(reinterpret_cast<const D*>(c.slot.od) + s * ob + (k - LR<D>::CAP));
                 }
             }
-            __syncthreads();
+            // no barrier: thread t reads only its own staged entry before the
+            // block scan inside process_local
             process_local<D, B>(a, c, sm, L, cnt, 0);
         }
+        // the bucket receives nothing while it is processed (insertions go
+        // to later buckets); the trailing barrier of process_local has been
+        // passed by every thread, and only thread 0 reads rn[s] next
         if (t == 0) L.rn[s] = 0;
-        __syncthreads();
     }
+#ifdef PPSP_PHASE_CLOCKS
+    if (t < 16) atomicAdd(&g_phase_clk[t], (unsigned long long)sm.ph_acc[t]);
+#endif
     // entries left behind by the disconnected exit: clear the ring and spills
     if (sm.lspill) {
         for (u32 w = t; w < nwords; w += B) c.slot.bm[0][w] = 0u;
@@ -1165,7 +1297,13 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
             sm.pb[t] = a.g.pc[s.pot_b];
         }
     }
-    if (sm.pcached) {
+    if (G.mode == GM_SSSP) {
+        // SSSP groups have no partners: the cache holds the targets instead
+        if (t == 0) sm.pcached = (G.qcnt <= PCAP) ? 1u : 0u;
+        __syncthreads();
+        if (sm.pcached)
+            for (u32 k = t; k < G.qcnt; k += B) sm.pcache[k] = PartnerDev{a.qedges[G.qbeg + k].b, G.qbeg + k};
+    } else if (sm.pcached) {
         const SearchDev s0 = a.searches[G.sbeg];
         const SearchDev sl = a.searches[G.sbeg + G.scnt - 1];
         const u32 np = sl.pbeg + sl.pcnt - s0.pbeg;
@@ -1273,7 +1411,9 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
             sm.dir0 = ld_volatile(&S[cur].cnt_dir[0]);
             sm.dir1 = ld_volatile(&S[cur].cnt_dir[1]);
             sm.mu0 = ldcg64(a.mu + G.qbeg);
-            sm.cert = (u32)(ldcg64(&S[cur].bmax) <= sm.minkey_in && G.mode != GM_SSSP);
+            const u64 bm = ldcg64(&S[cur].bmax);
+            sm.cert = (u32)(bm <= sm.minkey_in);
+            if (G.mode == GM_SSSP && bm < sm.bound[0]) sm.bound[0] = bm;
         }
         __syncthreads();
         const u32 count = sm.count;
@@ -1371,7 +1511,10 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
         }
         // flush per-CTA step results
         __syncthreads();
-        if (t == 0 && tc.rank == 0) {
+        if (G.mode == GM_SSSP && tc.rank == 0 && t < 32) {
+            const u64 m = sssp_target_max<D, B>(a, c, sm);
+            if (t == 0) S[nxt].bmax = (m == 0) ? INF64 : m;
+        } else if (t == 0 && tc.rank == 0) {
             u64 bmax = 0;
             for (u32 i = 0; i < G.scnt && bmax != INF64; ++i) {
                 u64 b;
@@ -1393,6 +1536,17 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
         }
         if (!team_sync(tc, a, &sm.flag)) return false;
         dense_cur = c.dense_nxt;
+    }
+
+    // ---- SSSP-based batches (Sec. 4.3): every query of the group reads its
+    // other endpoint's final distance from the single search ----
+    if (G.mode == GM_SSSP && G.qcnt > 0) {
+        for (u32 q = tc.rank * B + t; q < G.qcnt; q += tc.size * B) {
+            const QEdgeDev e = a.qedges[G.qbeg + q];
+            const u64 d = ld_dist(c.dist + flat_of(G, c.n, e.b, 0));
+            a.mu[G.qbeg + q] = (d == DT<D>::INF) ? INF64 : d;
+        }
+        if (!team_sync(tc, a, &sm.flag)) return false;
     }
 
     // ---- paths (optional), before the distances are reset ----
@@ -1592,3 +1746,15 @@ ppsp_status launch_scatter(const u32* d_map, const u64* d_mu, u64 k, u64* d_out,
 }
 
 }  // namespace ppsp
+
+#ifdef PPSP_PHASE_CLOCKS
+// Profiling builds only: copy (and optionally clear) the 16 phase cycle totals.
+extern "C" int ppsp_debug_phase_clocks(unsigned long long* out16, int clear) {
+    cudaError_t e = cudaMemcpyFromSymbol(out16, ppsp::g_phase_clk, 16 * sizeof(unsigned long long));
+    if (e == cudaSuccess && clear) {
+        static const unsigned long long zero[16] = {0};
+        e = cudaMemcpyToSymbol(ppsp::g_phase_clk, zero, sizeof(zero));
+    }
+    return (int)e;
+}
+#endif

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(MLP_H) mlp_infer_kernel(const float* P, const 
         const float y = mlp_forward_sample(P, Wb, feats + s * MLP_NF, s_x, s_h1, s_h2, s_red, false, &z1, &z2);
         if (threadIdx.x == 0) {
             if (y_out) y_out[s] = y;
-            if (groups) {
+            if (groups && groups[s].mode != GM_SSSP) {  // SSSP groups keep the default
                 float yc = fminf(fmaxf(y, ymin), ymax);
                 const double base = (double)delta_default;
                 double dd = floor(base * exp2((double)yc) + 0.5);

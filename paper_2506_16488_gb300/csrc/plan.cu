@@ -2,8 +2,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <numeric>
 #include <unordered_map>
+#include <unordered_set>
 
 #include "graph_impl.h"
 #include "mlp_internal.h"
@@ -67,6 +69,152 @@ struct UF {
     }
 };
 
+// Minimum vertex cover of a graph of at most 32 vertices given as adjacency
+// bit masks, by branch and bound: take the vertex v of largest uncovered
+// degree and branch on "v in the cover" / "all uncovered neighbours of v in
+// the cover"; a greedy maximal matching of the uncovered edges bounds the
+// rest from below (every matching edge needs its own cover vertex), and once
+// no vertex has two uncovered edges the remaining edges form a matching.
+void vc_exact(const std::vector<u32>& adj, u32 cover, u32 size, u32& best_size, u32& best) {
+    if (size >= best_size) return;
+    const u32 nv = (u32)adj.size();
+    u32 v = 0, maxd = 0;
+    for (u32 u = 0; u < nv; ++u) {
+        if (cover >> u & 1u) continue;
+        const u32 d = (u32)__builtin_popcount(adj[u] & ~cover);
+        if (d > maxd) {
+            maxd = d;
+            v = u;
+        }
+    }
+    if (maxd <= 1) {
+        u32 c = cover, sz = size;
+        for (u32 u = 0; u < nv; ++u)
+            if (!(c >> u & 1u) && (adj[u] & ~c)) {
+                c |= 1u << u;
+                ++sz;
+            }
+        if (sz < best_size) {
+            best_size = sz;
+            best = c;
+        }
+        return;
+    }
+    u32 m = cover, lb = 0;
+    for (u32 u = 0; u < nv; ++u) {
+        if (m >> u & 1u) continue;
+        const u32 w = adj[u] & ~m;
+        if (w) {
+            m |= (1u << u) | (w & (0u - w));
+            ++lb;
+        }
+    }
+    if (size + lb >= best_size) return;
+    vc_exact(adj, cover | (1u << v), size + 1, best_size, best);
+    const u32 nb = adj[v] & ~cover;
+    vc_exact(adj, cover | nb, size + (u32)__builtin_popcount(nb), best_size, best);
+}
+
+// Vertex cover of the query graph (Sec. 4.3): exact for components of at most
+// 32 vertices, greedy by uncovered degree otherwise.  Returns in[v] for the
+// local vertex ids 0..nv-1.
+std::vector<char> vertex_cover(u32 nv, const std::vector<std::pair<u32, u32>>& E) {
+    std::vector<u32> comp(nv);
+    std::iota(comp.begin(), comp.end(), 0u);
+    std::function<u32(u32)> find = [&](u32 x) { return comp[x] == x ? x : comp[x] = find(comp[x]); };
+    for (auto& e : E) comp[find(e.first)] = find(e.second);
+    std::unordered_map<u32, std::vector<u32>> cv;
+    std::unordered_map<u32, std::vector<std::pair<u32, u32>>> ce;
+    for (u32 v = 0; v < nv; ++v) cv[find(v)].push_back(v);
+    for (auto& e : E) ce[find(e.first)].push_back(e);
+    std::vector<char> in(nv, 0);
+    for (auto& kv : cv) {
+        auto& verts = kv.second;
+        auto& edges = ce[kv.first];
+        if (edges.empty()) continue;
+        if (verts.size() <= 32) {
+            std::unordered_map<u32, u32> loc;
+            for (u32 i = 0; i < verts.size(); ++i) loc[verts[i]] = i;
+            std::vector<u32> adj(verts.size(), 0u);
+            for (auto& e : edges) {
+                const u32 x = loc[e.first], y = loc[e.second];
+                adj[x] |= 1u << y;
+                adj[y] |= 1u << x;
+            }
+            u32 best = (verts.size() == 32) ? ~0u : ((1u << verts.size()) - 1u), best_size = (u32)verts.size();
+            vc_exact(adj, 0u, 0, best_size, best);
+            for (u32 i = 0; i < verts.size(); ++i) in[verts[i]] = (char)(best >> i & 1u);
+        } else {
+            std::vector<char> covered(edges.size(), 0);
+            size_t left = edges.size();
+            while (left) {
+                std::unordered_map<u32, u32> deg;
+                for (size_t k = 0; k < edges.size(); ++k)
+                    if (!covered[k]) {
+                        ++deg[edges[k].first];
+                        ++deg[edges[k].second];
+                    }
+                u32 pick = 0, pd = 0;
+                for (auto& d : deg)
+                    if (d.second > pd || (d.second == pd && d.first < pick)) {
+                        pick = d.first;
+                        pd = d.second;
+                    }
+                in[pick] = 1;
+                for (size_t k = 0; k < edges.size(); ++k)
+                    if (!covered[k] && (edges[k].first == pick || edges[k].second == pick)) {
+                        covered[k] = 1;
+                        --left;
+                    }
+            }
+        }
+    }
+    return in;
+}
+
+// Source of the single-source search that answers each query (s, t) of an
+// SSSP-based batch (Sec. 4.3): s itself for Plain-SSSP, the endpoint in the
+// vertex cover of G_q for VC-SSSP (s when both are in it).
+std::vector<u32> sssp_sources(int strategy, const std::vector<std::pair<u32, u32>>& uq) {
+    const u32 U = (u32)uq.size();
+    std::vector<u32> src(U);
+    if (strategy != PPSP_BATCH_VC) {
+        for (u32 u = 0; u < U; ++u) src[u] = uq[u].first;
+        return src;
+    }
+    std::unordered_map<u32, u32> vid;
+    std::vector<u32> verts;
+    auto get = [&](u32 v) {
+        auto it = vid.find(v);
+        if (it != vid.end()) return it->second;
+        vid.emplace(v, (u32)verts.size());
+        verts.push_back(v);
+        return (u32)verts.size() - 1;
+    };
+    std::vector<std::pair<u32, u32>> le(U);
+    for (u32 u = 0; u < U; ++u) le[u] = {get(uq[u].first), get(uq[u].second)};
+    const std::vector<char> in = vertex_cover((u32)verts.size(), le);
+    for (u32 u = 0; u < U; ++u) src[u] = in[le[u].first] ? uq[u].first : uq[u].second;
+    return src;
+}
+
+// AUTO strategy: smallest number of targets that makes a source's queries
+// one multi-target search (ET / A* modes).
+constexpr u32 AUTO_MIN_TARGETS = 4;
+
+// AUTO strategy, per connected component of G_q with nv vertices, ne edges
+// and a vertex cover of `cover` vertices.  With BiD-A* potentials a pair
+// search settles far fewer vertices than an unpruned or shared search (the
+// potential is only exact for isolated pairs, so shared searches lose it):
+// components run as independent pairs unless one vertex covers the whole
+// component (a star), whose one search from the centre answers every query.
+// Without potentials, a cover of at most a quarter of the vertices runs as
+// VC-SSSP (stars, forks), the rest as Multi-BiDS (Sec. 4.2 / 4.3).
+int auto_component(bool pot_pairs, u32 nv, u32 ne, u32 cover) {
+    if (pot_pairs) return (cover == 1 && ne >= AUTO_MIN_TARGETS) ? PPSP_BATCH_VC : PPSP_BATCH_PLAIN_STAR;
+    return (4u * cover <= nv) ? PPSP_BATCH_VC : PPSP_BATCH_MULTI;
+}
+
 u32 ceil_log2(u32 x) {
     u32 s = 0;
     while ((1u << s) < x) ++s;
@@ -80,7 +228,10 @@ ppsp_status check_options(const ppsp_graph* g, const ppsp_options& o) {
         return PPSP_ERR_INVALID_ARG;
     if (o.frontier < PPSP_FRONTIER_AUTO || o.frontier > PPSP_FRONTIER_DENSE) return PPSP_ERR_INVALID_ARG;
     if (o.layout < PPSP_LAYOUT_AUTO || o.layout > PPSP_LAYOUT_STACKED) return PPSP_ERR_INVALID_ARG;
-    if (o.batch_strategy < PPSP_BATCH_MULTI || o.batch_strategy > PPSP_BATCH_PLAIN) return PPSP_ERR_INVALID_ARG;
+    if (o.batch_strategy < PPSP_BATCH_MULTI || o.batch_strategy > PPSP_BATCH_AUTO) return PPSP_ERR_INVALID_ARG;
+    if (o.batch_strategy == PPSP_BATCH_VC && !g->info.undirected) return PPSP_ERR_UNSUPPORTED;
+    if ((o.batch_strategy == PPSP_BATCH_SSSP || o.batch_strategy == PPSP_BATCH_VC) && o.want_paths)
+        return PPSP_ERR_UNSUPPORTED;
     if (o.team_ctas < 0 || o.big_team_ctas < 0 || o.max_ctas < 0) return PPSP_ERR_INVALID_ARG;
     const bool astar = o.mode == PPSP_BIDASTAR || o.mode == PPSP_ASTAR;
     if (astar && !g->info.has_coords) return PPSP_ERR_NO_COORDS;
@@ -134,7 +285,10 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     for (u64 q = 0; q < k; ++q) {
         u32 s = pairs[2 * q], t = pairs[2 * q + 1];
         if (s == t) continue;  // d(s, s) = 0, no search
-        u64 key = bidir ? (((u64)std::min(s, t) << 32) | std::max(s, t)) : (((u64)s << 32) | t);
+        // Plain-SSSP searches from every query's own source (ordered pairs)
+        const bool unordered = (bidir && strategy != PPSP_BATCH_SSSP) || strategy == PPSP_BATCH_VC ||
+                               (strategy == PPSP_BATCH_AUTO && g->info.undirected);
+        u64 key = unordered ? (((u64)std::min(s, t) << 32) | std::max(s, t)) : (((u64)s << 32) | t);
         auto it = qe_id.find(key);
         if (it == qe_id.end()) {
             it = qe_id.emplace(key, (u32)uq.size()).first;
@@ -147,14 +301,53 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     // ---- groups ----
     // Each group: list of vertices (searches) and list of unique-query indices.
     std::vector<std::vector<u32>> gverts, gqueries;
-    if (!bidir || strategy != PPSP_BATCH_MULTI) {
-        for (u32 u = 0; u < U; ++u) {
-            if (bidir)
-                gverts.push_back({uq[u].first, uq[u].second});
-            else
-                gverts.push_back({uq[u].first});
-            gqueries.push_back({u});
+    std::vector<char> gsssp;                // group is one SSSP-based search (Sec. 4.3)
+    std::vector<u32> sssp_src(U, NONE);  // SSSP groups: the search answering each query
+    // one SSSP group per distinct source of the queries in `qs`
+    auto add_sssp_groups = [&](const std::vector<u32>& qs) {
+        std::unordered_map<u32, u32> gid;
+        for (u32 u : qs) {
+            auto it = gid.find(sssp_src[u]);
+            if (it == gid.end()) {
+                it = gid.emplace(sssp_src[u], (u32)gverts.size()).first;
+                gverts.push_back({sssp_src[u]});
+                gqueries.push_back({});
+                gsssp.push_back(1);
+            }
+            gqueries[it->second].push_back(u);
         }
+    };
+    auto add_single = [&](u32 u) {
+        if (bidir)
+            gverts.push_back({uq[u].first, uq[u].second});
+        else
+            gverts.push_back({uq[u].first});
+        gqueries.push_back({u});
+        gsssp.push_back(0);
+    };
+    if (strategy == PPSP_BATCH_SSSP || strategy == PPSP_BATCH_VC) {
+        // Sec. 4.3: one single-source search per selected source
+        sssp_src = sssp_sources(strategy, uq);
+        std::vector<u32> all(U);
+        std::iota(all.begin(), all.end(), 0u);
+        add_sssp_groups(all);
+    } else if (strategy == PPSP_BATCH_AUTO && !bidir) {
+        // one search per target, except sources with several targets, which
+        // get one search that stops when all of them are settled
+        std::unordered_map<u32, u32> per_src;
+        for (u32 u = 0; u < U; ++u) ++per_src[uq[u].first];
+        std::vector<u32> multi_t;
+        for (u32 u = 0; u < U; ++u) {
+            if (per_src[uq[u].first] >= AUTO_MIN_TARGETS && !o.want_paths) {
+                sssp_src[u] = uq[u].first;
+                multi_t.push_back(u);
+            } else {
+                add_single(u);
+            }
+        }
+        add_sssp_groups(multi_t);
+    } else if (!bidir || (strategy != PPSP_BATCH_MULTI && strategy != PPSP_BATCH_AUTO)) {
+        for (u32 u = 0; u < U; ++u) add_single(u);
     } else {
         // Multi-BiDS: V_q = distinct endpoints, components of G_q (Sec. 4.2)
         std::unordered_map<u32, u32> vid;
@@ -181,7 +374,35 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
             }
             it->second.push_back(u);
         }
+        const bool pot_pairs = o.mode == PPSP_BIDASTAR && g->info.has_coords;
         for (u32 r : comp_order) {
+            const std::vector<u32>& ce = comp_edges[r];
+            if (strategy == PPSP_BATCH_AUTO && ce.size() > 1) {
+                // the cheaper of Multi-BiDS, VC-SSSP and Plain* for this component
+                std::unordered_map<u32, u32> cl;
+                std::vector<std::pair<u32, u32>> cle;
+                for (u32 u : ce) {
+                    const u32 a = cl.emplace(le[u].first, (u32)cl.size()).first->second;
+                    const u32 b = cl.emplace(le[u].second, (u32)cl.size()).first->second;
+                    cle.emplace_back(a, b);
+                }
+                const std::vector<char> in = vertex_cover((u32)cl.size(), cle);
+                u32 cover = 0;
+                for (char x : in) cover += x ? 1u : 0u;
+                int pick = auto_component(pot_pairs, (u32)cl.size(), (u32)ce.size(), cover);
+                if (pick == PPSP_BATCH_VC && o.want_paths)  // SSSP groups record no paths
+                    pick = pot_pairs ? PPSP_BATCH_PLAIN_STAR : PPSP_BATCH_MULTI;
+                if (pick == PPSP_BATCH_VC) {
+                    for (u32 j = 0; j < ce.size(); ++j)
+                        sssp_src[ce[j]] = in[cle[j].first] ? uq[ce[j]].first : uq[ce[j]].second;
+                    add_sssp_groups(ce);
+                    continue;
+                }
+                if (pick == PPSP_BATCH_PLAIN_STAR) {
+                    for (u32 u : ce) add_single(u);
+                    continue;
+                }
+            }
             // split components with more than KMAX vertices into sub-groups
             std::vector<u32> cur_v, cur_q;
             std::unordered_map<u32, u32> in_cur;
@@ -191,6 +412,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
                 if (cur_v.size() + need > (size_t)KMAX) {
                     gverts.push_back(cur_v);
                     gqueries.push_back(cur_q);
+                    gsssp.push_back(0);
                     cur_v.clear();
                     cur_q.clear();
                     in_cur.clear();
@@ -204,6 +426,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
             }
             gverts.push_back(cur_v);
             gqueries.push_back(cur_q);
+            gsssp.push_back(0);
         }
     }
 
@@ -220,7 +443,11 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         G.qbeg = (u32)P->qedges.size();
         G.qcnt = (u32)Q.size();
         G.delta = delta;
-        if (bidir) {
+        const bool sssp = gsssp[gi] != 0;
+        if (sssp) {
+            G.mode = GM_SSSP;
+            G.target = NONE;
+        } else if (bidir) {
             G.mode = GM_BIDIR;
             G.target = NONE;
         } else {
@@ -246,17 +473,23 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
             u32 qe = G.qbeg + qi;
             uq_to_qe[u] = qe;
             QEdgeDev e;
-            e.a = local[uq[u].first];
-            e.b = bidir ? local[uq[u].second] : e.a;
+            if (sssp) {
+                // one search; b holds the query's other endpoint (a vertex id)
+                e.a = 0;
+                e.b = (uq[u].first == sssp_src[u]) ? uq[u].second : uq[u].first;
+            } else {
+                e.a = local[uq[u].first];
+                e.b = bidir ? local[uq[u].second] : e.a;
+            }
             P->qedges.push_back(e);
             P->qedge_ends.emplace_back(uq[u].first, uq[u].second);
-            if (bidir) {
+            if (bidir && !sssp) {
                 plist[e.a].push_back(PartnerDev{e.b, qe});
                 plist[e.b].push_back(PartnerDev{e.a, qe});
             }
             i64 h = g->info.has_coords ? pot_h_host(g, uq[u].first, uq[u].second) : 1;
             hmax[e.a] = std::max(hmax[e.a], h);
-            hmax[e.b] = std::max(hmax[e.b], h);
+            if (!sssp) hmax[e.b] = std::max(hmax[e.b], h);
         }
         for (u32 i = 0; i < G.scnt; ++i) {
             SearchDev s{};
@@ -267,7 +500,9 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
             s.pot = 0;
             s.pot_b = V[i];
             s.key_off = 0;
-            if (o.mode == PPSP_BIDASTAR && G.scnt == 2) {
+            if (sssp) {
+                // no pruning, no potential
+            } else if (o.mode == PPSP_BIDASTAR && G.scnt == 2) {
                 // Sec. 3.5 for an isolated pair: rho_i = h_partner - h_self, so the
                 // two searches use exactly opposite potentials (h_F = -h_B, which
                 // Theorem 3.4 relies on).  Searches of larger query-graph components
@@ -276,12 +511,14 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
                 s.pot = 1;
                 s.pot_b = V[plist[i][0].j];
                 s.key_off = -pot_h_host(g, s.pot_b, s.src);
-            } else if (o.mode == PPSP_ASTAR) {
+            } else if (o.mode == PPSP_ASTAR && !sssp) {
                 s.pot_b = G.target;
                 s.key_off = -pot_h_host(g, G.target, s.src);
             }
             P->searches.push_back(s);
-            work += (double)(hmax[i] + 1) * (double)(hmax[i] + 1) / 4.0;
+            // estimated settled area: a disc of radius hmax / 2 per search of a
+            // pruned bidirectional group, of radius hmax for an SSSP group
+            work += (double)(hmax[i] + 1) * (double)(hmax[i] + 1) / (sssp ? 1.0 : 4.0);
         }
         gwork[gi] = work;
         P->groups.push_back(G);
@@ -319,6 +556,8 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
                                 (double)G.scnt, (double)G.qcnt, 2.0 * G.qcnt / std::max<u32>(1, G.scnt)};
         for (int f = 0; f < 12; ++f) P->feats[(size_t)gi * 12 + f] = (float)std::log2(1.0 + std::max(0.0, raw[f]));
     }
+    // the models were trained on pair and Multi-BiDS groups: the inference
+    // kernel leaves SSSP groups at the default increment
     if (o.delta == 0 && g->delta_model[o.mode] != nullptr) P->model = g->delta_model[o.mode];
 
     // ---- launch shape ----
@@ -702,6 +941,34 @@ ppsp_status ppsp_plan_group_times(ppsp_plan* p, uint64_t* out_ns, uint64_t cap, 
     }
     if (!p->groups.empty())
         PPSP_CUDA_TRY(cudaMemcpy(out_ns, p->args.group_ns, p->groups.size() * 8, cudaMemcpyDeviceToHost));
+    return PPSP_OK;
+}
+
+ppsp_status ppsp_batch_sources(const uint32_t* pairs, uint64_t k, int32_t strategy, uint32_t* src_out,
+                               uint64_t* n_sources) {
+    if ((k && !pairs) || (k && !src_out) || !n_sources) return PPSP_ERR_INVALID_ARG;
+    if (strategy != PPSP_BATCH_SSSP && strategy != PPSP_BATCH_VC) return PPSP_ERR_INVALID_ARG;
+    // the same deduplication as the plan: unordered pairs for VC-SSSP
+    // (undirected graphs), ordered pairs for Plain-SSSP
+    std::unordered_map<u64, u32> qe_id;
+    std::vector<std::pair<u32, u32>> uq;
+    std::vector<u32> map(k, NONE);
+    for (u64 q = 0; q < k; ++q) {
+        const u32 s = pairs[2 * q], t = pairs[2 * q + 1];
+        if (s == t) continue;
+        const u64 key = (strategy == PPSP_BATCH_VC) ? (((u64)std::min(s, t) << 32) | std::max(s, t))
+                                                    : (((u64)s << 32) | t);
+        auto it = qe_id.find(key);
+        if (it == qe_id.end()) {
+            it = qe_id.emplace(key, (u32)uq.size()).first;
+            uq.emplace_back(s, t);
+        }
+        map[q] = it->second;
+    }
+    const std::vector<u32> src = sssp_sources(strategy, uq);
+    std::unordered_set<u32> distinct(src.begin(), src.end());
+    for (u64 q = 0; q < k; ++q) src_out[q] = (map[q] == NONE) ? NONE : src[map[q]];
+    *n_sources = distinct.size();
     return PPSP_OK;
 }
 

@@ -28,7 +28,7 @@ STATUS_NAMES = ["OK", "INVALID_ARG", "BAD_GRAPH", "OOM", "CUDA", "TIMEOUT", "NO_
 MODES = {"bids": 0, "bidastar": 1, "et": 2, "astar": 3}
 FRONTIER = {"auto": 0, "sparse": 1, "dense": 2}
 LAYOUT = {"auto": 0, "interleaved": 1, "stacked": 2}
-STRATEGY = {"multi": 0, "plain_star": 1, "plain": 2}
+STRATEGY = {"multi": 0, "plain_star": 1, "plain": 2, "sssp": 3, "vc": 4, "auto": 5}
 UNDIRECTED = 1
 DEBUG_BARRIER_NEVER_RELEASES = 1
 MLP_FEATURES = 12
@@ -130,6 +130,7 @@ def load(build_if_missing: bool = False):
             "ppsp_plan_features": (S, [p, p, u64, p]),
             "ppsp_plan_group_times": (S, [p, p, u64, p]),
             "ppsp_plan_uses_graph": (S, [p, p]),
+            "ppsp_batch_sources": (S, [p, u64, i32, p, p]),
             "ppsp_delta_model_create": (S, [p, p]),
             "ppsp_delta_model_destroy": (None, [p]),
             "ppsp_delta_model_get_params": (S, [p, p]),
@@ -157,6 +158,20 @@ def _check(status: int, what: str):
 
 def _ptr(a: Optional[np.ndarray]):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def batch_sources(pairs, strategy: str | int = "vc") -> tuple:
+    """Sources of an SSSP-based batch (Sec. 4.3), computed on the host:
+    (per-pair source vertex, 0xFFFFFFFF where s == t; number of distinct
+    sources).  strategy "sssp" = each query's own source, "vc" = an endpoint in
+    a vertex cover of the query graph."""
+    pa = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+    k = pa.shape[0]
+    out = np.zeros(max(1, k), dtype=np.uint32)
+    n = ctypes.c_uint64(0)
+    st = STRATEGY[strategy] if isinstance(strategy, str) else int(strategy)
+    _check(load().ppsp_batch_sources(_ptr(pa), k, st, _ptr(out), ctypes.byref(n)), "ppsp_batch_sources")
+    return out[:k], int(n.value)
 
 
 def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, frontier="auto",
