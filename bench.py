@@ -107,6 +107,13 @@ WORKLOAD_NAMES = {
 }
 
 
+METRIC = "PPSP queries/sec (exact distances), batched vs plain one-at-a-time"
+
+
+def workload_name(cfg: int, g, k: int, mode: str) -> str:
+    return "%s (%d vertices, %d CSR entries, %d queries per step), %s" % (WORKLOAD_NAMES[cfg], g.n, g.m, k, mode)
+
+
 def load_workload(cfg: int):
     from workloads import config_workload
 
@@ -169,9 +176,17 @@ def cpu_baseline(g, pairs, labels, budget_s: float = 20.0):
     t0 = time.perf_counter()
     oracle.pairs_threaded(g.offsets, g.targets, g.weights, sample, threads)
     dt = time.perf_counter() - t0
+    # single-threaded on a third of the sample (same strata), which also
+    # counts the edges Dijkstra scans (the work ratio's denominator)
+    sub = sample[::3]
+    t0 = time.perf_counter()
+    _, scanned = oracle.pairs(g.offsets, g.targets, g.weights, sub, return_scanned=True)
+    dt1 = time.perf_counter() - t0
     return {"value": sample.shape[0] / dt, "unit": "queries/s", "cores": threads, "kind": "oracle",
-            "sample": f"{sample.shape[0]} queries ({per} near/mid/far each) of the 1,000, one Dijkstra "
-                      f"per query, {threads} threads"}
+            "sample": f"{sample.shape[0]} queries ({per} per stratum: near/mid/far, or each batch pattern), "
+                      f"one Dijkstra per query, {threads} threads",
+            "single_thread_qps": sub.shape[0] / dt1,
+            "dijkstra_edges_per_query": scanned / max(1, sub.shape[0])}
 
 
 def run_reference(args):
@@ -201,11 +216,11 @@ def run_reference(args):
     total = sum(times)
     value = nq / total
     line = {
-        "impl": "reference", "metric": "PPSP queries/sec (exact distances)", "value": value,
+        "impl": "reference", "metric": METRIC, "value": value,
         "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "road-like 1024x1024 grid, 1000 near/mid/far queries",
+        "config": {"workload": workload_name(args.config, g, pairs.shape[0], mode),
                    "sample_per_step": int(idx.shape[0])},
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle",
                          "sample": f"{idx.shape[0]} stratified queries per step, binary-heap Dijkstra, "
@@ -251,8 +266,7 @@ def run_ours(args):
         sel = np.linspace(0, pairs.shape[0] - 1, args.queries).astype(np.int64)
         pairs, labels = pairs[sel], labels[sel]
     k = pairs.shape[0]
-    workload = "%s (%d vertices, %d CSR entries, %d queries per step), %s" % (
-        WORKLOAD_NAMES[args.config], g.n, g.m, k, mode)
+    workload = workload_name(args.config, g, k, mode)
     if args.max_ctas:
         workload += f", at most {args.max_ctas} CTAs"
     G = ppsp.Graph.from_csr(g)
@@ -394,7 +408,7 @@ def run_ours(args):
     achieved = alg_bytes / (ms_per_step / 1000.0) / 1e9
     cpu = cpu_baseline(g, pairs, labels) if world == 1 else None
     line = {
-        "metric": "PPSP queries/sec (exact distances), batched vs plain one-at-a-time",
+        "metric": METRIC,
         "value": qps,
         "unit": "queries/s",
         "n_gpus": world,
@@ -412,6 +426,10 @@ def run_ours(args):
                    "inputs": "plan (query graph, schedule) built before the timed region; graph, plan and "
                              "output resident in HBM", "parallelism": f"replicas x{world}"},
         "gteps": cnt["edges"] / (ms_per_step / 1000.0) / 1e9,
+        # edges scanned per query, GPU batch mean over the oracle's Dijkstra on
+        # the stratified sample
+        "work_ratio": (cnt["edges"] / k) / cpu["dijkstra_edges_per_query"]
+        if cpu and cpu.get("dijkstra_edges_per_query") else None,
         "plain": plain,
         "plain_same_delta": plain_same,
         "speedup_vs_plain": qps / world / plain["value"],

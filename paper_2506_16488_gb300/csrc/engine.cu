@@ -165,6 +165,17 @@ __device__ bool team_sync(const TeamCtx& tc, const EngineArgs& a, u32* s_flag) {
 constexpr u32 QSTAGE = 1024;  // staged frontier appends per CTA and tile
 constexpr u32 TSTAGE = 512;   // staged touched-list appends per CTA and tile
 constexpr u32 PCAP = 1024;    // partner entries of a group cached in shared memory
+// relaxations of a pair group each thread keeps in flight (one-CTA path)
+#ifndef PPSP_RELAX_ILP
+#define PPSP_RELAX_ILP 2
+#endif
+
+// Edges of a tile up to OWN_MULT * B find their entry in a shared-memory
+// owner table instead of a binary search over the degree prefix sums, when no
+// entry of the tile has more than OWN_MAXDEG edges (so that filling the table
+// costs each thread a few stores).
+constexpr u32 OWN_MULT = 4;
+constexpr u32 OWN_MAXDEG = 32;
 
 template <int B>
 struct Smem {
@@ -172,9 +183,12 @@ struct Smem {
     u32 flat[B];
     u32 beg[B];
     u32 pre[B];
+    unsigned short own[OWN_MULT * B];  // entry of each edge of the tile (see OWN_MULT)
+    u32 own_off;                       // a tile entry has more than OWN_MAXDEG edges (set by the scan)
     u64 d[B];
     unsigned char si[B];
     u32 wsum[B / 32];
+    u32 wbig[B / 32];
     // staging of appends
     u32 qbuf[QSTAGE];
     u32 tbuf[TSTAGE];
@@ -236,7 +250,7 @@ __device__ unsigned long long g_phase_clk[16];
 #endif
 
 template <int B>
-__device__ __forceinline__ u32 block_excl_scan(u32 x, Smem<B>& sm, u32* total) {
+__device__ __forceinline__ u32 block_excl_scan(u32 x, Smem<B>& sm, u32* total, bool big = false) {
     const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     u32 incl = x;
 #pragma unroll
@@ -244,7 +258,11 @@ __device__ __forceinline__ u32 block_excl_scan(u32 x, Smem<B>& sm, u32* total) {
         u32 y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= (u32)o) incl += y;
     }
-    if (lane == 31) sm.wsum[wid] = incl;
+    const u32 wbig = __any_sync(0xffffffffu, big) ? 1u : 0u;
+    if (lane == 31) {
+        sm.wsum[wid] = incl;
+        sm.wbig[wid] = wbig;
+    }
     __syncthreads();
     if (wid == 0) {
         u32 s = (lane < B / 32) ? sm.wsum[lane] : 0;
@@ -256,10 +274,35 @@ __device__ __forceinline__ u32 block_excl_scan(u32 x, Smem<B>& sm, u32* total) {
         }
         if (lane < B / 32) sm.wsum[lane] = si - s;  // exclusive warp offsets
         if (lane == B / 32 - 1) sm.total = si;
+        // some entry of the tile has more edges than the owner table handles
+        const bool any = __any_sync(0xffffffffu, lane < B / 32 && sm.wbig[lane] != 0);
+        if (lane == 0) sm.own_off = any ? 1u : 0u;
     }
     __syncthreads();
     *total = sm.total;
     return sm.wsum[wid] + incl - x;
+}
+
+// After the degree scan (before its closing barrier): thread t records itself
+// as the owner of its edges excl .. excl + deg - 1 that fall in the table.
+template <int B>
+__device__ __forceinline__ void write_owner(Smem<B>& sm, u32 t, u32 excl, u32 deg) {
+    if (deg > OWN_MAXDEG) return;  // the tile falls back to the binary search
+    const u32 end = min(excl + deg, OWN_MULT * (u32)B);
+    for (u32 e = excl; e < end; ++e) sm.own[e] = (unsigned short)t;
+}
+
+// Entry of edge e of the tile: the owner table, or the largest j with
+// pre[j] <= e.
+template <int B>
+__device__ __forceinline__ u32 edge_owner(const Smem<B>& sm, u32 e, u32 cnt) {
+    if (e < OWN_MULT * (u32)B && !sm.own_off) return sm.own[e];
+    u32 lo = 0, hi = cnt;
+    while (hi - lo > 1) {
+        const u32 mid = (lo + hi) >> 1;
+        if (sm.pre[mid] <= e) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
 // ----------------------------------------------------------------------------
@@ -575,15 +618,12 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
         }
     }
     u32 total;
-    u32 excl = block_excl_scan<B>(deg, sm, &total);
+    u32 excl = block_excl_scan<B>(deg, sm, &total, deg > OWN_MAXDEG);
     sm.pre[t] = (t < cnt) ? excl : total;
+    if (deg) write_owner<B>(sm, t, excl, deg);
     __syncthreads();
     for (u32 e = t; e < total; e += B) {
-        u32 lo = 0, hi = cnt;
-        while (hi - lo > 1) {
-            u32 mid = (lo + hi) >> 1;
-            if (sm.pre[mid] <= e) lo = mid; else hi = mid;
-        }
+        const u32 lo = edge_owner<B>(sm, e, cnt);
         const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
         const uint2 ew = __ldg(a.g.edges + edge);
         ++c.c_e;
@@ -832,15 +872,16 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
     }
     PH_MARK(sm, 1);  // staging + extraction of thread 0's entry
     u32 total;
-    const u32 excl = block_excl_scan<B>(deg, sm, &total);
+    const u32 excl = block_excl_scan<B>(deg, sm, &total, deg > OWN_MAXDEG);
     sm.pre[t] = (t < cnt) ? excl : total;
+    if (deg) write_owner<B>(sm, t, excl, deg);
     __syncthreads();
     PH_MARK(sm, 2);  // scan, including the wait for the slowest extraction
     if (c.pair) {
         // pair groups: RX edges per thread at a time, their loads and atomics
         // issued together (instruction-level parallelism on the dependent
         // edge -> distance -> atomicMin chain)
-        constexpr int RX = 4;
+        constexpr int RX = PPSP_RELAX_ILP;
         for (u32 e0 = t; e0 < total; e0 += RX * B) {
             u32 v2[RX], si[RX], f2[RX];
             u64 nd[RX], own[RX], oth[RX], old[RX];
@@ -854,11 +895,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
                 nd[k] = DT<D>::INF;
                 si[k] = 0;
                 if (ok[k]) {
-                    u32 lo = 0, hi = cnt;
-                    while (hi - lo > 1) {
-                        const u32 mid = (lo + hi) >> 1;
-                        if (sm.pre[mid] <= e) lo = mid; else hi = mid;
-                    }
+                    const u32 lo = edge_owner<B>(sm, e, cnt);
                     const uint2 ew = __ldg(a.g.edges + sm.beg[lo] + (e - sm.pre[lo]));
                     v2[k] = ew.x;
                     si[k] = sm.si[lo];
@@ -915,11 +952,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
         }
     } else {
         for (u32 e = t; e < total; e += B) {
-            u32 lo = 0, hi = cnt;
-            while (hi - lo > 1) {
-                const u32 mid = (lo + hi) >> 1;
-                if (sm.pre[mid] <= e) lo = mid; else hi = mid;
-            }
+            const u32 lo = edge_owner<B>(sm, e, cnt);
             const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
             const uint2 ew = __ldg(a.g.edges + edge);
             ++c.c_e;
