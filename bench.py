@@ -476,11 +476,14 @@ def run_serving(args):
         G.set_delta_model(mode, model)
     free, total = torch.cuda.mem_get_info()
     budget = int(0.6 * free)
-    lanes = 4
-    lane_ctas = max(1, (2 * torch.cuda.get_device_properties(0).multi_processor_count) // lanes)
+    # the engine keeps one CTA per SM resident: the lanes split the SMs, and
+    # every query of a micro-batch runs on one CTA (the bucketed one-CTA path)
+    lanes = args.lanes
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    lane_ctas = args.lane_ctas or max(1, sms // lanes)
     rng = np.random.default_rng(5003)
     src = lambda k: g.lcc[rng.integers(0, g.lcc.shape[0], size=(k, 2))]
-    ex = GpuExecutor(G, lanes, mode=mode, dist_bits=64, lane_ctas=lane_ctas)
+    ex = GpuExecutor(G, lanes, mode=mode, dist_bits=64, lane_ctas=lane_ctas, team_ctas=args.team_ctas)
     # warm-up: slot pool and code paths
     serve(poisson_arrivals(2000, 0.2, src, seed=5004), ex, Scheduler(lanes, 256, budget, memory_model(g.n, lane_ctas, 64)))
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
@@ -501,7 +504,7 @@ def run_serving(args):
         "ms_per_step": 1000.0 * args.duration, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"{WORKLOAD_NAMES[5]} ({g.n} vertices, {g.m} CSR entries)", "lanes": lanes,
-                   "lane_ctas": lane_ctas, "memory_budget_bytes": budget,
+                   "lane_ctas": lane_ctas, "team_ctas": args.team_ctas or "auto", "memory_budget_bytes": budget,
                    "delta": "learned MLP" if model is not None else "default (mean edge weight)"},
         "rates": rates, "clocks": clocks,
         "e2e": {"value": best["sustained_qps"], "unit": "queries/s", "h2d_bytes_per_step": None,
@@ -532,6 +535,9 @@ def main():
                     help="serving (config 5): offered query rates")
     ap.add_argument("--duration", type=float, default=2.0, help="serving (config 5): seconds per rate")
     ap.add_argument("--small", action="store_true", help="serving (config 5): small graph (tests)")
+    ap.add_argument("--lanes", type=int, default=8, help="serving (config 5): concurrent micro-batches")
+    ap.add_argument("--lane-ctas", type=int, default=0, help="serving (config 5): CTAs per lane (0 = SMs / lanes)")
+    ap.add_argument("--team-ctas", type=int, default=1, help="serving (config 5): CTAs per query (0 = auto)")
     args = ap.parse_args()
     if args.impl != "reference" and args.config == 5:
         run_serving(args)

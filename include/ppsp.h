@@ -122,7 +122,15 @@ typedef struct {
     uint32_t debug_flags;    /* test hooks, 0 in normal use (PPSP_DEBUG_*)                  */
     uint32_t cuda_graph;     /* plans: 1 = capture the launches of ppsp_plan_run into a CUDA
                                 graph on a non-NULL stream and replay it (default 0)         */
-    uint32_t reserved[6];
+    uint32_t stepping_rho;   /* GetDist variant (Sec. 2: Delta*-stepping, rho-stepping and
+                                Bellman-Ford are all stepping algorithms).  0 (default):
+                                one Delta-bucket per step.  rho > 0: a step of a one-CTA
+                                group takes consecutive non-empty buckets until they hold
+                                at least rho entries (with Delta small this approaches
+                                rho-stepping, which extracts the rho smallest keys; with
+                                Delta huge every step takes the whole frontier, which is
+                                Bellman-Ford).  Groups on several CTAs ignore it.            */
+    uint32_t reserved[5];
 } ppsp_options;
 
 /* Test hook: device barriers wait for one arrival that never comes, so every

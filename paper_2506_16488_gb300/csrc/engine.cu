@@ -170,6 +170,8 @@ constexpr u32 PCAP = 1024;    // partner entries of a group cached in shared mem
 #define PPSP_RELAX_ILP 2
 #endif
 
+constexpr u32 LR_NB = 32;  // buckets in the one-CTA ring
+
 // Edges of a tile up to OWN_MULT * B find their entry in a shared-memory
 // owner table instead of a binary search over the degree prefix sums, when no
 // entry of the tile has more than OWN_MAXDEG edges (so that filling the table
@@ -206,6 +208,9 @@ struct Smem {
     u32 pcached, pot_any;
     // one-CTA bucketed frontier (run_local)
     u64 lstep, lcur, llate;
+    u64 lfirst;         // first bucket of the step (lcur is its last; more than one with rho)
+    u32 lpre[LR_NB];    // entries in buckets cur + 1 .. cur + j of the ring (lpre[0] = 0)
+    u32 lj0, ljl;       // the step's buckets, relative to the previous step's last bucket
     u64 lfar_min[2];
     u32 lfar_n[2];
     u32 lfar_fb, lfar_tgt, lspill, tov;
@@ -646,10 +651,13 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
 // when the ring's window reaches them); an entry that finds its bucket or the
 // far list full sets its bit in the slot's spill bitmap and is recovered from
 // its current distance when nothing else is left.
+#ifndef PPSP_RING_CAP
+#define PPSP_RING_CAP 256
+#endif
 template <typename D>
 struct LR {
-    static constexpr u32 NB = 32;                          // buckets in the ring
-    static constexpr u32 CAP = sizeof(D) == 4 ? 256 : 128;  // shared-memory entries per bucket
+    static constexpr u32 NB = LR_NB;                       // buckets in the ring
+    static constexpr u32 CAP = sizeof(D) == 4 ? PPSP_RING_CAP : PPSP_RING_CAP / 2;  // shared-memory entries per bucket
     static constexpr size_t bytes() { return (size_t)NB * CAP * (4 + sizeof(D)) + NB * 4; }
 };
 
@@ -688,7 +696,8 @@ __device__ __forceinline__ void insert_local(GCtx<D>& c, Smem<B>& sm, const Loca
         atomicMin(reinterpret_cast<unsigned long long*>(&sm.llate), (unsigned long long)key);
     }
     bool stored = false;
-    if (b < cur + LR<D>::NB) {
+    // ring slots of the buckets of this step are not reused until it ends
+    if (b < sm.lfirst + LR<D>::NB) {
         const u32 s = (u32)(b % LR<D>::NB);
         // one shared-memory atomic per bucket per warp
         cg::coalesced_group peers = cg::labeled_partition(cg::coalesced_threads(), (int)s);
@@ -1037,6 +1046,7 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
     if (t == 0) {
         sm.lstep = (G.mode == GM_BIDIR) ? 2 * G.delta : G.delta;
         sm.lcur = 0;
+        sm.lfirst = 0;
         sm.lfar_fb = 0;
         sm.lfar_tgt = 0;
         sm.lfar_n[0] = sm.lfar_n[1] = 0;
@@ -1070,9 +1080,19 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
         }
         if (t < 32) {
             const u64 cur = sm.lcur;
-            const bool full = t >= 1 && t < LR<D>::NB && L.rn[(u32)((cur + t) % LR<D>::NB)] != 0;
-            const u32 mask = __ballot_sync(0xffffffffu, full);
+            const u32 ob = c.slot.ocap / LR<D>::NB;
+            u32 cnt = 0;
+            if (t >= 1 && t < LR<D>::NB) cnt = min(L.rn[(u32)((cur + t) % LR<D>::NB)], LR<D>::CAP + ob);
+            const u32 mask = __ballot_sync(0xffffffffu, cnt != 0);
             if (mask) rb = cur + (u32)(__ffs(mask) - 1);
+            u32 incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (t >= (u32)o) incl += y;
+            }
+            sm.lpre[t] = incl;  // entries in buckets cur + 1 .. cur + t
+            __syncwarp();
         }
         if (t == 0) {
             sm.flag = 0;  // 0 = process lcur, 1 = redistribute, 2 = recover, 3 = done
@@ -1105,10 +1125,25 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
                                        (sm.lfar_n[fb] > c.slot.qcap / 2 && sm.lfar_n[fb] > 2 * sm.lfar_after))) {
                 // far entries due soon, an empty ring, or a far list filling up
                 // with stale entries (re-bucketing drops them)
-                if (fm <= rb && fm > cur + 1) sm.lcur = fm - 1;
+                if (fm <= rb && fm > cur + 1) sm.lcur = sm.lfirst = fm - 1;
                 sm.flag = 1;
             } else if (rb != INF64) {
-                sm.lcur = rb;
+                // the step takes bucket rb, and with rho the following ones
+                // while the entries before them number fewer than rho (never a
+                // bucket the far list reaches)
+                const u32 j0 = (u32)(rb - cur);
+                u32 jl = j0;
+                if (a.rho) {
+                    const u32 base = sm.lpre[j0 - 1];
+                    for (u32 j = j0 + 1; j < LR<D>::NB; ++j) {
+                        if (sm.lpre[j - 1] - base >= a.rho || cur + j >= fm) break;
+                        if (sm.lpre[j] != sm.lpre[j - 1]) jl = j;
+                    }
+                }
+                sm.lj0 = j0;
+                sm.ljl = jl;
+                sm.lfirst = rb;
+                sm.lcur = cur + jl;
             } else if (sm.lspill) {
                 sm.flag = 2;
             } else {
@@ -1146,15 +1181,23 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
             PH_MARK(sm, 6);
             continue;
         }
-        // process bucket lcur: theta = lcur * step
+        // process buckets lfirst .. lcur (theta = lcur * step) as one list:
+        // bucket cur0 + j holds entries lpre[j - 1] .. lpre[j] - 1 of the
+        // ring window counted from the previous step's last bucket cur0
         ++rounds;
-        const u32 s = (u32)(sm.lcur % LR<D>::NB);
+        const u32 j0 = sm.lj0, jl = sm.ljl;
+        const u64 cur0 = sm.lfirst - j0;
         const u32 ob = c.slot.ocap / LR<D>::NB;
-        const u32 n = min(L.rn[s], LR<D>::CAP + ob);
+        const u32 pbase = sm.lpre[j0 - 1];
+        const u32 n = sm.lpre[jl] - pbase;
         for (u32 base = 0; base < n; base += B) {
             const u32 cnt = min((u32)B, n - base);
             if (t < cnt) {
-                const u32 k = base + t;
+                const u32 e = base + t;
+                u32 j = j0;
+                while (sm.lpre[j] - pbase <= e) ++j;  // at most jl (e < n)
+                const u32 k = e - (sm.lpre[j - 1] - pbase);
+                const u32 s = (u32)((cur0 + j) % LR<D>::NB);
                 if (k < LR<D>::CAP) {
                     sm.flat[t] = L.rf[s * LR<D>::CAP + k];
                     sm.d[t] = (u64)L.rd[s * LR<D>::CAP + k];
@@ -1167,10 +1210,13 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
             // block scan inside process_local
             process_local<D, B>(a, c, sm, L, cnt, 0);
         }
-        // the bucket receives nothing while it is processed (insertions go
+        // the buckets receive nothing while they are processed (insertions go
         // to later buckets); the trailing barrier of process_local has been
-        // passed by every thread, and only thread 0 reads rn[s] next
-        if (t == 0) L.rn[s] = 0;
+        // passed by every thread, and only thread 0 reads rn next
+        if (t == 0) {
+            for (u32 j = j0; j <= jl; ++j) L.rn[(u32)((cur0 + j) % LR<D>::NB)] = 0;
+            sm.lfirst = sm.lcur;  // the insertion window starts after this step
+        }
     }
 #ifdef PPSP_PHASE_CLOCKS
     if (t < 16) atomicAdd(&g_phase_clk[t], (unsigned long long)sm.ph_acc[t]);

@@ -322,6 +322,17 @@ ppsp_status ppsp_graph_create(uint64_t n, uint64_t m, const uint64_t* offsets, c
         cudaGetLastError();
         return PPSP_ERR_CUDA;
     }
+    {
+        // plans take their descriptor arenas from the device's stream-ordered
+        // pool; keep up to 1 GiB of freed pool memory mapped between plans
+        // instead of returning it at every synchronisation (this process only)
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, g->device) == cudaSuccess) {
+            uint64_t keep = 1ull << 30;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
     auto fail = [&](cudaError_t e, const char* what) {
         set_last_cuda_error(e, what, __FILE__, __LINE__);
         cudaGetLastError();

@@ -245,8 +245,10 @@ ppsp_status check_options(const ppsp_graph* g, const ppsp_options& o) {
 static void plan_free_partial(ppsp_plan* P) {
     for (Slot* x : P->slots) slot_release(P->g, x);
     P->slots.clear();
-    cudaFree(P->d_arena);
-    cudaFree(P->d_paths);
+    // stream-ordered frees: no device-wide synchronisation, so plans on other
+    // streams keep running (the serving loop closes plans while others run)
+    if (P->d_arena) cudaFreeAsync(P->d_arena, P->stream);
+    if (P->d_paths) cudaFreeAsync(P->d_paths, P->stream);
     P->d_arena = nullptr;
     P->d_paths = nullptr;
     cudaGetLastError();
@@ -686,7 +688,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     size_t o_gns = take(P->groups.size() * 8);
     P->runstate_bytes = off - o_run;
     P->arena_bytes = off;
-    cudaError_t ce = cudaMalloc(&P->d_arena, P->arena_bytes);
+    cudaError_t ce = cudaMallocAsync(&P->d_arena, P->arena_bytes, P->stream);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         for (Slot* x : P->slots) slot_release(g, x);
@@ -712,9 +714,11 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     put(o_q1, P->queue_items[1].data(), P->queue_items[1].size() * 4);
     put(o_map, P->map.data(), k * 4);
     put(o_feat, P->feats.data(), P->feats.size() * 4);
-    ce = cudaMemcpy(base, h.data(), static_bytes, cudaMemcpyHostToDevice);
+    // pageable source: staged before the call returns, so h may go out of scope
+    ce = cudaMemcpyAsync(base, h.data(), static_bytes, cudaMemcpyHostToDevice, P->stream);
     if (ce != cudaSuccess) {
         cudaGetLastError();
+        plan_free_partial(P.get());
         return PPSP_ERR_CUDA;
     }
 
@@ -739,6 +743,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     a.queue_head = (u32*)(base + o_qh);
     a.dense_den = o.dense_den ? o.dense_den : 16u;
     a.frontier = (u32)o.frontier;
+    a.rho = o.stepping_rho;
     a.debug = o.debug_flags;
     a.spin_limit = o.spin_limit ? o.spin_limit : (1ull << 26);
     a.err = (u32*)(base + o_err);
@@ -758,7 +763,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         const size_t b_off = ((NQ + 1) * 8 + 255) & ~(size_t)255;
         const size_t b_len = (NQ * 8 + 255) & ~(size_t)255;
         const size_t b_meet = (NQ * 4 + 255) & ~(size_t)255;
-        ce = cudaMalloc(&P->d_paths, std::max<size_t>(256, b_buf + b_off + b_len + b_meet));
+        ce = cudaMallocAsync(&P->d_paths, std::max<size_t>(256, b_buf + b_off + b_len + b_meet), P->stream);
         if (ce != cudaSuccess) {
             cudaGetLastError();
             plan_free_partial(P.get());
@@ -770,7 +775,8 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         a.path_len = (u64*)(pb + b_buf + b_off);
         P->d_meet = (u32*)(pb + b_buf + b_off + b_len);
         a.meet = P->d_meet;
-        ce = cudaMemcpy((void*)a.path_off, P->path_off.data(), (NQ + 1) * 8, cudaMemcpyHostToDevice);
+        ce = cudaMemcpyAsync((void*)a.path_off, P->path_off.data(), (NQ + 1) * 8, cudaMemcpyHostToDevice,
+                             P->stream);
         if (ce != cudaSuccess) {
             cudaGetLastError();
             plan_free_partial(P.get());
@@ -790,8 +796,8 @@ static void plan_free(ppsp_plan* P) {
         cudaDeviceSynchronize();
     for (Slot* s : P->slots) slot_release(P->g, s);
     if (P->gexec) cudaGraphExecDestroy(P->gexec);
-    cudaFree(P->d_arena);
-    cudaFree(P->d_paths);
+    if (P->d_arena) cudaFreeAsync(P->d_arena, P->stream);
+    if (P->d_paths) cudaFreeAsync(P->d_paths, P->stream);
     cudaGetLastError();
     delete P;
 }
@@ -871,8 +877,9 @@ static ppsp_status plan_wait(ppsp_plan* P, ppsp_counters* counters) {
     }
     u32 err = 0;
     EngineCounters ec{};
-    PPSP_CUDA_TRY(cudaMemcpy(&err, P->args.err, 4, cudaMemcpyDeviceToHost));
-    PPSP_CUDA_TRY(cudaMemcpy(&ec, P->args.counters, sizeof(ec), cudaMemcpyDeviceToHost));
+    PPSP_CUDA_TRY(cudaMemcpyAsync(&err, P->args.err, 4, cudaMemcpyDeviceToHost, P->stream));
+    PPSP_CUDA_TRY(cudaMemcpyAsync(&ec, P->args.counters, sizeof(ec), cudaMemcpyDeviceToHost, P->stream));
+    PPSP_CUDA_TRY(cudaStreamSynchronize(P->stream));
     if (counters) {
         memset(counters, 0, sizeof(*counters));
         counters->extracted = ec.extracted;
@@ -1003,7 +1010,7 @@ static ppsp_status run_host(ppsp_graph* g, const uint32_t* pairs, uint64_t k, co
     ppsp_status st = plan_create_impl(g, pairs, k, opt, single, &P, hp ? caps.data() : nullptr);
     if (st != PPSP_OK) return st;
     u64* d_out = nullptr;
-    cudaError_t ce = cudaMalloc(&d_out, std::max<u64>(1, k) * 8);
+    cudaError_t ce = cudaMallocAsync((void**)&d_out, std::max<u64>(1, k) * 8, P->stream);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         plan_free(P);
@@ -1012,7 +1019,8 @@ static ppsp_status run_host(ppsp_graph* g, const uint32_t* pairs, uint64_t k, co
     st = plan_launch(P, d_out);
     if (st == PPSP_OK) st = plan_wait(P, counters);
     if (st == PPSP_OK && k) {
-        ce = cudaMemcpy(dists_out, d_out, k * 8, cudaMemcpyDeviceToHost);
+        ce = cudaMemcpyAsync(dists_out, d_out, k * 8, cudaMemcpyDeviceToHost, P->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(P->stream);
         if (ce != cudaSuccess) {
             cudaGetLastError();
             st = PPSP_ERR_CUDA;
@@ -1025,9 +1033,11 @@ static ppsp_status run_host(ppsp_graph* g, const uint32_t* pairs, uint64_t k, co
         std::vector<u64> plen(NQ, 0);
         std::vector<u32> pbuf(P->path_off[NQ]);
         if (NQ) {
-            ce = cudaMemcpy(plen.data(), P->args.path_len, NQ * 8, cudaMemcpyDeviceToHost);
+            ce = cudaMemcpyAsync(plen.data(), P->args.path_len, NQ * 8, cudaMemcpyDeviceToHost, P->stream);
             if (ce == cudaSuccess && !pbuf.empty())
-                ce = cudaMemcpy(pbuf.data(), P->args.path_buf, pbuf.size() * 4, cudaMemcpyDeviceToHost);
+                ce = cudaMemcpyAsync(pbuf.data(), P->args.path_buf, pbuf.size() * 4, cudaMemcpyDeviceToHost,
+                                     P->stream);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(P->stream);
             if (ce != cudaSuccess) {
                 cudaGetLastError();
                 st = PPSP_ERR_CUDA;
@@ -1057,7 +1067,7 @@ static ppsp_status run_host(ppsp_graph* g, const uint32_t* pairs, uint64_t k, co
         }
         if (st == PPSP_OK && small) st = PPSP_ERR_BUFFER_TOO_SMALL;
     }
-    cudaFree(d_out);
+    cudaFreeAsync(d_out, P->stream);
     plan_free(P);
     return st;
 }

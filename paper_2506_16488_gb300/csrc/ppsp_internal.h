@@ -139,6 +139,7 @@ struct EngineArgs {
     // options
     u32 dense_den;        // dense when count > flat_size / dense_den (0 = never)
     u32 frontier;         // PPSP_FRONTIER_*
+    u32 rho;              // one-CTA path: a step takes buckets until it holds >= rho entries (0 = one)
     u32 debug;
     u64 spin_limit;
     u32* err;

@@ -53,7 +53,8 @@ class Options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("debug_flags", ctypes.c_uint32),
         ("cuda_graph", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 6),
+        ("stepping_rho", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 5),
     ]
 
 
@@ -178,7 +179,7 @@ def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, 
                  layout="auto", strategy="multi", block_threads: int = 0, team_ctas: int = 0,
                  big_team_ctas: int = 0, dense_den: int = 0, want_paths: bool = False, max_ctas: int = 0,
                  spin_limit: int = 0, stream: int | None = None, debug_flags: int = 0,
-                 cuda_graph: bool = False) -> Options:
+                 cuda_graph: bool = False, stepping_rho: int = 0) -> Options:
     o = Options()
     load().ppsp_options_init(ctypes.byref(o))
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
@@ -197,6 +198,7 @@ def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, 
     o.stream = stream
     o.debug_flags = debug_flags
     o.cuda_graph = int(bool(cuda_graph))
+    o.stepping_rho = stepping_rho
     return o
 
 

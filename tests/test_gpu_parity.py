@@ -328,3 +328,29 @@ def test_tiny_random_graphs_one_cta(seed):
                 got = G.batch(pairs, mode=mode, strategy=strategy, team_ctas=1, big_team_ctas=1,
                               delta=int(rng.integers(1, 3000)))
                 assert np.array_equal(got, want), (mode, strategy)
+
+
+@pytest.mark.parametrize("rho", [1, 64, 512, 10 ** 6])
+@pytest.mark.parametrize("delta", [1, 0, 300, 10 ** 9])
+def test_stepping_rho_merges_buckets(cfg1, rho, delta):
+    # GetDist variants (Sec. 2): a step takes buckets until it holds >= rho
+    # entries; rho = 10^6 with a huge Delta is Bellman-Ford.  Any schedule
+    # returns d(s, t) (Theorems 3.3/3.4).
+    g, pairs, want, G = cfg1
+    for mode in ("bids", "bidastar", "et", "astar"):
+        got = G.batch(pairs, mode=mode, team_ctas=1, big_team_ctas=1, stepping_rho=rho, delta=delta)
+        assert np.array_equal(got, want), (mode, rho, delta)
+
+
+@pytest.mark.parametrize("rho", [32, 4096])
+def test_stepping_rho_road_far_list_and_spills(rho):
+    g = road_like_graph(160, seed=77)
+    pairs, _ = near_mid_far_pairs(g, 60, seed=78)
+    pairs = np.concatenate([pairs, clique_pairs(g, 6, 79), star_pairs(g, 12, 80)])
+    want = oracle.pairs(g.offsets, g.targets, g.weights, pairs)
+    with ppsp.Graph.from_csr(g) as G:
+        for delta in (1, 0, 10 ** 9):
+            for strategy in ("multi", "auto"):
+                got = G.batch(pairs, mode="bidastar", strategy=strategy, team_ctas=1, big_team_ctas=1,
+                              stepping_rho=rho, delta=delta)
+                assert np.array_equal(got, want), (delta, strategy)
