@@ -82,7 +82,8 @@ enum {
                                   query source; answers read from its distances          */
     PPSP_BATCH_VC = 4,         /* VC-SSSP (Sec. 4.3): single-source searches only from a
                                   vertex cover of G_q (exact up to 32 vertices per
-                                  component, greedy above); undirected graphs.  For both
+                                  component, greedy above; directed graphs: a minimum
+                                  bipartite cover, targets searching backward).  For both
                                   SSSP strategies a search stops once every one of its
                                   targets is settled (no remaining key below the largest
                                   target distance, the multi-target form of ET's prune) */
@@ -186,7 +187,12 @@ const char* ppsp_last_error_detail(void);
  *   weights  host uint32[m]
  *   coords   host float[2n] (x, y per vertex) or NULL; needed by the A* modes
  *   flags    PPSP_UNDIRECTED: the CSR is symmetric with equal weights both ways
- *            (validated; the bidirectional modes search backwards on the same CSR)
+ *            (validated; the bidirectional modes search backwards on the same CSR).
+ *            Without it the graph is directed: the library also keeps its
+ *            transpose on the device (another 4(n+1) + 8m bytes), and a query's
+ *            target searches in-edges (Sec. 4.4: searches forward from sources,
+ *            backward from targets; Multi-BiDS groups pair them bipartitely).
+ *            VC-SSSP covers the bipartite query graph (Konig).
  * Inputs are copied; the caller may free them after the call.  On success
  * *out owns device memory until ppsp_graph_destroy.
  * Errors: INVALID_ARG (null pointers, n or m out of range), BAD_GRAPH
@@ -296,18 +302,25 @@ ppsp_status ppsp_plan_uses_graph(const ppsp_plan* p, int32_t* out);
 /* Source selection of the SSSP-based batch strategies (Sec. 4.3), host only
  * (no device work, usable without a GPU).
  *   pairs      host array of k (s, t) vertex-id pairs (uint32, row-major k x 2)
- *   strategy   PPSP_BATCH_SSSP (the source of each query) or PPSP_BATCH_VC
- *              (an endpoint in a vertex cover of the query graph: minimum by
+ *   strategy   PPSP_BATCH_SSSP (a forward search from the source of each
+ *              query) or PPSP_BATCH_VC (a search from an endpoint in a vertex
+ *              cover of the query graph)
+ *   flags      PPSP_UNDIRECTED for an undirected graph: the cover is minimum by
  *              exhaustive branch and bound for components of at most 32
- *              vertices, greedy by uncovered degree above)
+ *              vertices, greedy by uncovered degree above; 0 for a directed
+ *              graph: the query graph is bipartite (sources, targets) and the
+ *              cover is minimum (maximum matching and Konig's theorem), a
+ *              target in it searching backward
  *   src_out    host array of k: the vertex whose single-source search answers
  *              pair q, 0xFFFFFFFF for s == t (no search); caller-owned
- *   n_sources  number of distinct sources, i.e. full searches the plan runs
+ *   dir_out    host array of k or NULL: 0 = the search follows out-edges,
+ *              1 = in-edges (a backward search from the query's target)
+ *   n_sources  number of distinct (vertex, direction) searches the plan runs
  * This is exactly the selection ppsp_plan_create makes for these strategies.
  * Vertex ids are not range-checked (no graph). Errors: PPSP_ERR_INVALID_ARG for
  * null pointers or another strategy. */
-ppsp_status ppsp_batch_sources(const uint32_t* pairs, uint64_t k, int32_t strategy, uint32_t* src_out,
-                               uint64_t* n_sources);
+ppsp_status ppsp_batch_sources(const uint32_t* pairs, uint64_t k, int32_t strategy, uint32_t flags,
+                               uint32_t* src_out, uint32_t* dir_out, uint64_t* n_sources);
 
 /*
  * Learned stepping increment.  The paper tunes Delta of Delta*-stepping by

@@ -200,6 +200,7 @@ struct Smem {
     u32 pbeg[KMAX];
     u32 pcnt[KMAX];
     u32 pot[KMAX];
+    u32 sdir[KMAX];  // 0: out-edges (off / edges), 1: in-edges (off_t / edges_t)
     int2 pa[KMAX];
     int2 pb[KMAX];
     i64 key_off[KMAX];
@@ -308,6 +309,17 @@ __device__ __forceinline__ u32 edge_owner(const Smem<B>& sm, u32 e, u32 cnt) {
         if (sm.pre[mid] <= e) lo = mid; else hi = mid;
     }
     return lo;
+}
+
+// CSR rows a search follows: out-edges from a source, in-edges back from a
+// target (the same arrays for an undirected graph).
+template <int B>
+__device__ __forceinline__ const u32* rows(const EngineArgs& a, const Smem<B>& sm, u32 i) {
+    return sm.sdir[i] ? a.g.off_t : a.g.off;
+}
+template <int B>
+__device__ __forceinline__ const uint2* adj(const EngineArgs& a, const Smem<B>& sm, u32 i) {
+    return sm.sdir[i] ? a.g.edges_t : a.g.edges;
 }
 
 // ----------------------------------------------------------------------------
@@ -587,8 +599,9 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
         u32 v, i;
         decode_flat(c.G, c.n, f, v, i);
         // independent loads issued together: offsets, potential coordinates, distances
-        const u32 b0 = __ldg(a.g.off + v);
-        const u32 b1 = __ldg(a.g.off + v + 1);
+        const u32* off = rows<B>(a, sm, i);
+        const u32 b0 = __ldg(off + v);
+        const u32 b1 = __ldg(off + v + 1);
         int2 pv2 = make_int2(0, 0);
         if (sm.pot_any) pv2 = __ldg(a.g.pc + v);
         if (sparse_src) atomicAnd(bm_cur + (f >> 5), ~(1u << (f & 31u)));
@@ -630,7 +643,7 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
     for (u32 e = t; e < total; e += B) {
         const u32 lo = edge_owner<B>(sm, e, cnt);
         const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
-        const uint2 ew = __ldg(a.g.edges + edge);
+        const uint2 ew = __ldg(adj<B>(a, sm, sm.si[lo]) + edge);
         ++c.c_e;
         relax<D, B>(a, c, sm, sm.si[lo], sm.d[lo], ew);
     }
@@ -839,8 +852,9 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
         const u64 dins = sm.d[t];  // stored distance (INF: recover from the current one)
         u32 v, i;
         decode_flat(c.G, c.n, f, v, i);
-        const u32 b0 = __ldg(a.g.off + v);
-        const u32 b1 = (mode == 0) ? __ldg(a.g.off + v + 1) : b0;
+        const u32* off = rows<B>(a, sm, i);
+        const u32 b0 = __ldg(off + v);
+        const u32 b1 = (mode == 0) ? __ldg(off + v + 1) : b0;
         int2 pv2 = make_int2(0, 0);
         if (sm.pot_any) pv2 = __ldg(a.g.pc + v);
         u64 d, oth = DT<D>::INF;
@@ -905,7 +919,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
                 si[k] = 0;
                 if (ok[k]) {
                     const u32 lo = edge_owner<B>(sm, e, cnt);
-                    const uint2 ew = __ldg(a.g.edges + sm.beg[lo] + (e - sm.pre[lo]));
+                    const uint2 ew = __ldg(adj<B>(a, sm, sm.si[lo]) + sm.beg[lo] + (e - sm.pre[lo]));
                     v2[k] = ew.x;
                     si[k] = sm.si[lo];
                     nd[k] = sm.d[lo] + (u64)ew.y;
@@ -963,7 +977,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
         for (u32 e = t; e < total; e += B) {
             const u32 lo = edge_owner<B>(sm, e, cnt);
             const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
-            const uint2 ew = __ldg(a.g.edges + edge);
+            const uint2 ew = __ldg(adj<B>(a, sm, sm.si[lo]) + edge);
             ++c.c_e;
             relax_local<D, B>(a, c, sm, L, sm.si[lo], sm.d[lo], ew);
         }
@@ -1249,11 +1263,15 @@ __device__ u64 walk_back(const EngineArgs& a, GCtx<D>& c, const Smem<B>& sm, u32
             if (lane == 0) atomicOr(a.err, ERRB_INTERNAL);
             break;
         }
+        // the tight edges into x of a forward search are in-edges, those of
+        // a backward search (distances to its target) out-edges
         const u64 dx = ld_dist(c.dist + flat_of(c.G, c.n, x, i));
-        const u32 b0 = __ldg(a.g.off + x), b1 = __ldg(a.g.off + x + 1);
+        const u32* off = sm.sdir[i] ? a.g.off : a.g.off_t;
+        const uint2* edges = sm.sdir[i] ? a.g.edges : a.g.edges_t;
+        const u32 b0 = __ldg(off + x), b1 = __ldg(off + x + 1);
         u32 best = NONE;
         for (u32 e = b0 + lane; e < b1; e += 32) {
-            const uint2 ew = __ldg(a.g.edges + e);
+            const uint2 ew = __ldg(edges + e);
             const u64 du = ld_dist(c.dist + flat_of(c.G, c.n, ew.x, i));
             if (du != DT<D>::INF && du + ew.y == dx && ew.x < best) best = ew.x;
         }
@@ -1369,6 +1387,7 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
         sm.pbeg[t] = sm.pcached ? s.pbeg - p0 : s.pbeg;
         sm.pcnt[t] = s.pcnt;
         sm.pot[t] = s.pot;
+        sm.sdir[t] = s.dir;
         sm.key_off[t] = s.key_off;
         if (s.pot) atomicOr(&sm.pot_any, 1u);
         if (a.g.pc != nullptr) {

@@ -338,6 +338,8 @@ ppsp_status ppsp_graph_create(uint64_t n, uint64_t m, const uint64_t* offsets, c
         cudaGetLastError();
         cudaFree(g->d_off);
         cudaFree(g->d_edges);
+        cudaFree(g->d_off_t);
+        cudaFree(g->d_edges_t);
         cudaFree(g->d_pc);
         return e == cudaErrorMemoryAllocation ? PPSP_ERR_OOM : PPSP_ERR_CUDA;
     };
@@ -348,6 +350,25 @@ ppsp_status ppsp_graph_create(uint64_t n, uint64_t m, const uint64_t* offsets, c
     if (m && (ce = cudaMemcpy(g->d_edges, ed.data(), m * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(ce, "cudaMemcpy(edges)");
     info.device_bytes = (n + 1) * 4 + m * 8;
+    if (!info.undirected) {
+        // transpose (in-edges, each row sorted by source): backward searches
+        // from a target and path walks of forward searches follow it
+        std::vector<u32> offt(n + 1, 0);
+        for (u64 e = 0; e < m; ++e) ++offt[targets[e] + 1];
+        for (u64 v = 0; v < n; ++v) offt[v + 1] += offt[v];
+        std::vector<u32> fill(offt.begin(), offt.end() - 1);
+        std::vector<uint2> edt(m);
+        for (u64 u = 0; u < n; ++u)
+            for (u64 e = offsets[u]; e < offsets[u + 1]; ++e) edt[fill[targets[e]]++] = make_uint2((u32)u, weights[e]);
+        if ((ce = cudaMalloc(&g->d_off_t, (n + 1) * 4)) != cudaSuccess) return fail(ce, "cudaMalloc(off_t)");
+        if ((ce = cudaMalloc(&g->d_edges_t, std::max<u64>(1, m) * 8)) != cudaSuccess)
+            return fail(ce, "cudaMalloc(edges_t)");
+        if ((ce = cudaMemcpy(g->d_off_t, offt.data(), (n + 1) * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(ce, "cudaMemcpy(off_t)");
+        if (m && (ce = cudaMemcpy(g->d_edges_t, edt.data(), m * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(ce, "cudaMemcpy(edges_t)");
+        info.device_bytes += (n + 1) * 4 + m * 8;
+    }
     if (coords && g->pot_scale > 0.0) {
         std::vector<int2> pc(n);
         for (u64 v = 0; v < n; ++v) pc[v] = make_int2((int)g->pc_host[2 * v], (int)g->pc_host[2 * v + 1]);
@@ -374,6 +395,8 @@ void ppsp_graph_destroy(ppsp_graph* g) {
     g->pool.clear();
     cudaFree(g->d_off);
     cudaFree(g->d_edges);
+    cudaFree(g->d_off_t);
+    cudaFree(g->d_edges_t);
     cudaFree(g->d_pc);
     cudaFree(g->d_scratch_u32);
     cudaFree(g->d_scratch_i64);

@@ -39,6 +39,8 @@ struct ppsp_graph {
     uint64_t n = 0, m = 0;
     ppsp::u32* d_off = nullptr;
     uint2* d_edges = nullptr;
+    ppsp::u32* d_off_t = nullptr;  // transpose of a directed graph (null when undirected)
+    uint2* d_edges_t = nullptr;
     int2* d_pc = nullptr;
     std::vector<int64_t> pc_host;  // 2n potential coordinates
     double pot_scale = 0.0;
@@ -60,6 +62,8 @@ struct ppsp_graph {
         ppsp::GraphDev g;
         g.off = d_off;
         g.edges = d_edges;
+        g.off_t = d_off_t ? d_off_t : d_off;
+        g.edges_t = d_edges_t ? d_edges_t : d_edges;
         g.pc = d_pc;
         g.n = (ppsp::u32)n;
         g.pot_shift = (ppsp::u32)pot_shift;

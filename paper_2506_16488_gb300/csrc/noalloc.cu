@@ -119,8 +119,8 @@ __global__ void na_setup_kernel(unsigned char* base, u32 s, u32 t, u64 m, u64 de
     G->kshift = 1;
     G->delta = d;
     SearchDev* S = reinterpret_cast<SearchDev*>(base + O_SEARCH);
-    S[0] = SearchDev{s, 0, 1, 0, s, 0};
-    S[1] = SearchDev{t, 1, 1, 0, t, 0};
+    S[0] = SearchDev{s, 0, 1, 0, s, 0, 0, 0};
+    S[1] = SearchDev{t, 1, 1, 0, t, 1, 0, 0};
     PartnerDev* P = reinterpret_cast<PartnerDev*>(base + O_PART);
     P[0] = PartnerDev{1, 0};
     P[1] = PartnerDev{0, 0};
@@ -192,6 +192,8 @@ extern "C" ppsp_status ppsp_query_noalloc(const uint32_t* d_offsets, const uint3
     EngineArgs a{};
     a.g.off = d_offsets;
     a.g.edges = reinterpret_cast<const uint2*>(d_edges);
+    a.g.off_t = a.g.off;  // symmetric CSR: the transpose is the graph itself
+    a.g.edges_t = a.g.edges;
     a.g.pc = nullptr;
     a.g.n = n;
     a.g.pot_shift = 0;

@@ -172,14 +172,101 @@ std::vector<char> vertex_cover(u32 nv, const std::vector<std::pair<u32, u32>>& E
     return in;
 }
 
-// Source of the single-source search that answers each query (s, t) of an
-// SSSP-based batch (Sec. 4.3): s itself for Plain-SSSP, the endpoint in the
-// vertex cover of G_q for VC-SSSP (s when both are in it).
-std::vector<u32> sssp_sources(int strategy, const std::vector<std::pair<u32, u32>>& uq) {
+// Minimum vertex cover of a bipartite graph (left 0..nl-1, right
+// 0..nr-1): a maximum matching by augmenting paths, then Konig's
+// construction (left vertices not reachable by alternating paths from free
+// left vertices, right vertices reachable).  Returns cover flags.
+void bipartite_cover(u32 nl, u32 nr, const std::vector<std::pair<u32, u32>>& E, std::vector<char>& inl,
+                     std::vector<char>& inr) {
+    std::vector<std::vector<u32>> adjl(nl);
+    for (auto& e : E) adjl[e.first].push_back(e.second);
+    std::vector<u32> ml(nl, NONE), mr(nr, NONE);
+    std::vector<u32> seen(nr, NONE);
+    // iterative augmenting-path search from left vertex r0 (stamp = r0)
+    auto augment = [&](u32 r0) {
+        std::vector<std::pair<u32, u32>> st;  // (left vertex, next edge index)
+        std::vector<u32> via;                 // right vertex taken from each frame
+        st.emplace_back(r0, 0);
+        while (!st.empty()) {
+            auto& [x, k] = st.back();
+            if (k == adjl[x].size()) {
+                st.pop_back();
+                if (!via.empty()) via.pop_back();
+                continue;
+            }
+            const u32 y = adjl[x][k++];
+            if (seen[y] == r0) continue;
+            seen[y] = r0;
+            if (mr[y] == NONE) {
+                // flip the path: frames hold left vertices, via the right ones
+                via.push_back(y);
+                for (size_t f = st.size(); f-- > 0;) {
+                    const u32 lx = st[f].first, ry = via[f];
+                    ml[lx] = ry;
+                    mr[ry] = lx;
+                }
+                return true;
+            }
+            via.push_back(y);
+            st.emplace_back(mr[y], 0);
+        }
+        return false;
+    };
+    for (u32 x = 0; x < nl; ++x) augment(x);
+    // alternating reachability from free left vertices
+    std::vector<char> zl(nl, 0), zr(nr, 0);
+    std::vector<u32> queue;
+    for (u32 x = 0; x < nl; ++x)
+        if (ml[x] == NONE) {
+            zl[x] = 1;
+            queue.push_back(x);
+        }
+    for (size_t h = 0; h < queue.size(); ++h) {
+        const u32 x = queue[h];
+        for (u32 y : adjl[x])
+            if (!zr[y] && ml[x] != y) {
+                zr[y] = 1;
+                const u32 x2 = mr[y];
+                if (x2 != NONE && !zl[x2]) {
+                    zl[x2] = 1;
+                    queue.push_back(x2);
+                }
+            }
+    }
+    inl.assign(nl, 0);
+    inr.assign(nr, 0);
+    for (u32 x = 0; x < nl; ++x) inl[x] = zl[x] ? 0 : 1;
+    for (u32 y = 0; y < nr; ++y) inr[y] = zr[y] ? 1 : 0;
+}
+
+// Search that answers each query (s, t) of an SSSP-based batch (Sec. 4.3),
+// as (vertex, direction): Plain-SSSP searches forward from s; VC-SSSP from an
+// endpoint in a vertex cover of G_q: on an undirected graph (direction 0)
+// exact up to 32 vertices per component and greedy above; on a directed
+// graph G_q is bipartite (sources, targets: Sec. 4.4) and its minimum cover
+// comes from a maximum matching (Konig); a target in the cover searches
+// backward (direction 1) over the transpose.
+struct SrcDir {
+    u32 v;
+    u32 dir;
+};
+std::vector<SrcDir> sssp_sources(int strategy, bool directed, const std::vector<std::pair<u32, u32>>& uq) {
     const u32 U = (u32)uq.size();
-    std::vector<u32> src(U);
+    std::vector<SrcDir> src(U);
     if (strategy != PPSP_BATCH_VC) {
-        for (u32 u = 0; u < U; ++u) src[u] = uq[u].first;
+        for (u32 u = 0; u < U; ++u) src[u] = {uq[u].first, 0};
+        return src;
+    }
+    if (directed) {
+        std::unordered_map<u32, u32> lid, rid;
+        std::vector<std::pair<u32, u32>> E(U);
+        for (u32 u = 0; u < U; ++u)
+            E[u] = {lid.emplace(uq[u].first, (u32)lid.size()).first->second,
+                    rid.emplace(uq[u].second, (u32)rid.size()).first->second};
+        std::vector<char> inl, inr;
+        bipartite_cover((u32)lid.size(), (u32)rid.size(), E, inl, inr);
+        for (u32 u = 0; u < U; ++u)
+            src[u] = inl[E[u].first] ? SrcDir{uq[u].first, 0} : SrcDir{uq[u].second, 1};
         return src;
     }
     std::unordered_map<u32, u32> vid;
@@ -194,7 +281,7 @@ std::vector<u32> sssp_sources(int strategy, const std::vector<std::pair<u32, u32
     std::vector<std::pair<u32, u32>> le(U);
     for (u32 u = 0; u < U; ++u) le[u] = {get(uq[u].first), get(uq[u].second)};
     const std::vector<char> in = vertex_cover((u32)verts.size(), le);
-    for (u32 u = 0; u < U; ++u) src[u] = in[le[u].first] ? uq[u].first : uq[u].second;
+    for (u32 u = 0; u < U; ++u) src[u] = {in[le[u].first] ? uq[u].first : uq[u].second, 0};
     return src;
 }
 
@@ -229,14 +316,12 @@ ppsp_status check_options(const ppsp_graph* g, const ppsp_options& o) {
     if (o.frontier < PPSP_FRONTIER_AUTO || o.frontier > PPSP_FRONTIER_DENSE) return PPSP_ERR_INVALID_ARG;
     if (o.layout < PPSP_LAYOUT_AUTO || o.layout > PPSP_LAYOUT_STACKED) return PPSP_ERR_INVALID_ARG;
     if (o.batch_strategy < PPSP_BATCH_MULTI || o.batch_strategy > PPSP_BATCH_AUTO) return PPSP_ERR_INVALID_ARG;
-    if (o.batch_strategy == PPSP_BATCH_VC && !g->info.undirected) return PPSP_ERR_UNSUPPORTED;
     if ((o.batch_strategy == PPSP_BATCH_SSSP || o.batch_strategy == PPSP_BATCH_VC) && o.want_paths)
         return PPSP_ERR_UNSUPPORTED;
     if (o.team_ctas < 0 || o.big_team_ctas < 0 || o.max_ctas < 0) return PPSP_ERR_INVALID_ARG;
     const bool astar = o.mode == PPSP_BIDASTAR || o.mode == PPSP_ASTAR;
     if (astar && !g->info.has_coords) return PPSP_ERR_NO_COORDS;
     const bool bidir = o.mode == PPSP_BIDS || o.mode == PPSP_BIDASTAR;
-    if (bidir && !g->info.undirected) return PPSP_ERR_UNSUPPORTED;
     return PPSP_OK;
 }
 
@@ -288,8 +373,8 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         u32 s = pairs[2 * q], t = pairs[2 * q + 1];
         if (s == t) continue;  // d(s, s) = 0, no search
         // Plain-SSSP searches from every query's own source (ordered pairs)
-        const bool unordered = (bidir && strategy != PPSP_BATCH_SSSP) || strategy == PPSP_BATCH_VC ||
-                               (strategy == PPSP_BATCH_AUTO && g->info.undirected);
+        const bool unordered = g->info.undirected && ((bidir && strategy != PPSP_BATCH_SSSP) ||
+                                                      strategy == PPSP_BATCH_VC || strategy == PPSP_BATCH_AUTO);
         u64 key = unordered ? (((u64)std::min(s, t) << 32) | std::max(s, t)) : (((u64)s << 32) | t);
         auto it = qe_id.find(key);
         if (it == qe_id.end()) {
@@ -304,15 +389,21 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     // Each group: list of vertices (searches) and list of unique-query indices.
     std::vector<std::vector<u32>> gverts, gqueries;
     std::vector<char> gsssp;                // group is one SSSP-based search (Sec. 4.3)
-    std::vector<u32> sssp_src(U, NONE);  // SSSP groups: the search answering each query
+    // directed graphs: a query's source searches out-edges (direction 0), its
+    // target in-edges (direction 1); on undirected graphs every search is 0
+    const bool directed = !g->info.undirected;
+    std::vector<std::vector<unsigned char>> gdirs;
+    std::vector<SrcDir> sssp_src(U, SrcDir{NONE, 0});  // SSSP groups: the search answering each query
     // one SSSP group per distinct source of the queries in `qs`
     auto add_sssp_groups = [&](const std::vector<u32>& qs) {
-        std::unordered_map<u32, u32> gid;
+        std::unordered_map<u64, u32> gid;
         for (u32 u : qs) {
-            auto it = gid.find(sssp_src[u]);
+            const u64 key = ((u64)sssp_src[u].v << 1) | sssp_src[u].dir;
+            auto it = gid.find(key);
             if (it == gid.end()) {
-                it = gid.emplace(sssp_src[u], (u32)gverts.size()).first;
-                gverts.push_back({sssp_src[u]});
+                it = gid.emplace(key, (u32)gverts.size()).first;
+                gverts.push_back({sssp_src[u].v});
+                gdirs.push_back({(unsigned char)sssp_src[u].dir});
                 gqueries.push_back({});
                 gsssp.push_back(1);
             }
@@ -320,16 +411,19 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         }
     };
     auto add_single = [&](u32 u) {
-        if (bidir)
+        if (bidir) {
             gverts.push_back({uq[u].first, uq[u].second});
-        else
+            gdirs.push_back({0, (unsigned char)(directed ? 1 : 0)});
+        } else {
             gverts.push_back({uq[u].first});
+            gdirs.push_back({0});
+        }
         gqueries.push_back({u});
         gsssp.push_back(0);
     };
     if (strategy == PPSP_BATCH_SSSP || strategy == PPSP_BATCH_VC) {
         // Sec. 4.3: one single-source search per selected source
-        sssp_src = sssp_sources(strategy, uq);
+        sssp_src = sssp_sources(strategy, directed, uq);
         std::vector<u32> all(U);
         std::iota(all.begin(), all.end(), 0u);
         add_sssp_groups(all);
@@ -341,7 +435,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         std::vector<u32> multi_t;
         for (u32 u = 0; u < U; ++u) {
             if (per_src[uq[u].first] >= AUTO_MIN_TARGETS && !o.want_paths) {
-                sssp_src[u] = uq[u].first;
+                sssp_src[u] = {uq[u].first, 0};
                 multi_t.push_back(u);
             } else {
                 add_single(u);
@@ -351,18 +445,23 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     } else if (!bidir || (strategy != PPSP_BATCH_MULTI && strategy != PPSP_BATCH_AUTO)) {
         for (u32 u = 0; u < U; ++u) add_single(u);
     } else {
-        // Multi-BiDS: V_q = distinct endpoints, components of G_q (Sec. 4.2)
-        std::unordered_map<u32, u32> vid;
+        // Multi-BiDS: V_q = distinct endpoints, components of G_q (Sec. 4.2).
+        // On a directed graph V_q holds (vertex, role) pairs: a source searches
+        // forward, a target backward, so G_q is bipartite (Sec. 4.4).
+        std::unordered_map<u64, u32> vid;
         std::vector<u32> verts;
-        auto get = [&](u32 v) {
-            auto it = vid.find(v);
+        std::vector<unsigned char> vrole;
+        auto get = [&](u32 v, unsigned char role) {
+            const u64 key = directed ? (((u64)v << 1) | role) : (u64)v;
+            auto it = vid.find(key);
             if (it != vid.end()) return it->second;
-            vid.emplace(v, (u32)verts.size());
+            vid.emplace(key, (u32)verts.size());
             verts.push_back(v);
+            vrole.push_back(directed ? role : 0);
             return (u32)verts.size() - 1;
         };
         std::vector<std::pair<u32, u32>> le(U);
-        for (u32 u = 0; u < U; ++u) le[u] = {get(uq[u].first), get(uq[u].second)};
+        for (u32 u = 0; u < U; ++u) le[u] = {get(uq[u].first, 0), get(uq[u].second, 1)};
         UF uf((u32)verts.size());
         for (auto& e : le) uf.join(e.first, e.second);
         std::unordered_map<u32, std::vector<u32>> comp_edges;
@@ -395,8 +494,11 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
                 if (pick == PPSP_BATCH_VC && o.want_paths)  // SSSP groups record no paths
                     pick = pot_pairs ? PPSP_BATCH_PLAIN_STAR : PPSP_BATCH_MULTI;
                 if (pick == PPSP_BATCH_VC) {
+                    // on a directed graph the component is bipartite ((vertex,
+                    // role) pairs): a target in the cover searches backward
                     for (u32 j = 0; j < ce.size(); ++j)
-                        sssp_src[ce[j]] = in[cle[j].first] ? uq[ce[j]].first : uq[ce[j]].second;
+                        sssp_src[ce[j]] = in[cle[j].first] ? SrcDir{uq[ce[j]].first, 0}
+                                                           : SrcDir{uq[ce[j]].second, directed ? 1u : 0u};
                     add_sssp_groups(ce);
                     continue;
                 }
@@ -407,15 +509,18 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
             }
             // split components with more than KMAX vertices into sub-groups
             std::vector<u32> cur_v, cur_q;
+            std::vector<unsigned char> cur_d;
             std::unordered_map<u32, u32> in_cur;
             for (u32 u : comp_edges[r]) {
                 u32 a = le[u].first, b = le[u].second;
                 u32 need = (in_cur.count(a) ? 0 : 1) + (in_cur.count(b) ? 0 : 1);
                 if (cur_v.size() + need > (size_t)KMAX) {
                     gverts.push_back(cur_v);
+                    gdirs.push_back(cur_d);
                     gqueries.push_back(cur_q);
                     gsssp.push_back(0);
                     cur_v.clear();
+                    cur_d.clear();
                     cur_q.clear();
                     in_cur.clear();
                 }
@@ -423,10 +528,12 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
                     if (!in_cur.count(x)) {
                         in_cur.emplace(x, (u32)cur_v.size());
                         cur_v.push_back(verts[x]);
+                        cur_d.push_back(vrole[x]);
                     }
                 cur_q.push_back(u);
             }
             gverts.push_back(cur_v);
+            gdirs.push_back(cur_d);
             gqueries.push_back(cur_q);
             gsssp.push_back(0);
         }
@@ -465,8 +572,11 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         }
         const u64 range = G.layout == PPSP_LAYOUT_INTERLEAVED ? (n << G.kshift) : (u64)G.scnt * n;
         if (range >= 0xFFFFFFFFull) return PPSP_ERR_UNSUPPORTED;
-        std::unordered_map<u32, u32> local;
-        for (u32 i = 0; i < G.scnt; ++i) local.emplace(V[i], i);
+        const auto& Dv = gdirs[gi];
+        std::unordered_map<u64, u32> local;  // (vertex, direction) -> search
+        auto lkey = [](u32 v, unsigned char d) { return ((u64)v << 1) | d; };
+        for (u32 i = 0; i < G.scnt; ++i) local.emplace(lkey(V[i], Dv[i]), i);
+        const unsigned char tdir = directed ? 1 : 0;  // direction of a query's target search
         std::vector<std::vector<PartnerDev>> plist(G.scnt);
         std::vector<i64> hmax(G.scnt, 0);
         double work = 0.0;
@@ -478,10 +588,10 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
             if (sssp) {
                 // one search; b holds the query's other endpoint (a vertex id)
                 e.a = 0;
-                e.b = (uq[u].first == sssp_src[u]) ? uq[u].second : uq[u].first;
+                e.b = (uq[u].first == sssp_src[u].v && sssp_src[u].dir == 0) ? uq[u].second : uq[u].first;
             } else {
-                e.a = local[uq[u].first];
-                e.b = bidir ? local[uq[u].second] : e.a;
+                e.a = local[lkey(uq[u].first, 0)];
+                e.b = bidir ? local[lkey(uq[u].second, tdir)] : e.a;
             }
             P->qedges.push_back(e);
             P->qedge_ends.emplace_back(uq[u].first, uq[u].second);
@@ -496,6 +606,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         for (u32 i = 0; i < G.scnt; ++i) {
             SearchDev s{};
             s.src = V[i];
+            s.dir = Dv[i];
             s.pbeg = (u32)P->partners.size();
             s.pcnt = (u32)plist[i].size();
             for (auto& pd : plist[i]) P->partners.push_back(pd);
@@ -951,20 +1062,21 @@ ppsp_status ppsp_plan_group_times(ppsp_plan* p, uint64_t* out_ns, uint64_t cap, 
     return PPSP_OK;
 }
 
-ppsp_status ppsp_batch_sources(const uint32_t* pairs, uint64_t k, int32_t strategy, uint32_t* src_out,
-                               uint64_t* n_sources) {
+ppsp_status ppsp_batch_sources(const uint32_t* pairs, uint64_t k, int32_t strategy, uint32_t flags,
+                               uint32_t* src_out, uint32_t* dir_out, uint64_t* n_sources) {
     if ((k && !pairs) || (k && !src_out) || !n_sources) return PPSP_ERR_INVALID_ARG;
     if (strategy != PPSP_BATCH_SSSP && strategy != PPSP_BATCH_VC) return PPSP_ERR_INVALID_ARG;
-    // the same deduplication as the plan: unordered pairs for VC-SSSP
-    // (undirected graphs), ordered pairs for Plain-SSSP
+    // the same deduplication as the plan: unordered pairs for VC-SSSP on an
+    // undirected graph, ordered pairs otherwise
+    const bool directed = !(flags & PPSP_UNDIRECTED);
+    const bool unordered = !directed && strategy == PPSP_BATCH_VC;
     std::unordered_map<u64, u32> qe_id;
     std::vector<std::pair<u32, u32>> uq;
     std::vector<u32> map(k, NONE);
     for (u64 q = 0; q < k; ++q) {
         const u32 s = pairs[2 * q], t = pairs[2 * q + 1];
         if (s == t) continue;
-        const u64 key = (strategy == PPSP_BATCH_VC) ? (((u64)std::min(s, t) << 32) | std::max(s, t))
-                                                    : (((u64)s << 32) | t);
+        const u64 key = unordered ? (((u64)std::min(s, t) << 32) | std::max(s, t)) : (((u64)s << 32) | t);
         auto it = qe_id.find(key);
         if (it == qe_id.end()) {
             it = qe_id.emplace(key, (u32)uq.size()).first;
@@ -972,9 +1084,13 @@ ppsp_status ppsp_batch_sources(const uint32_t* pairs, uint64_t k, int32_t strate
         }
         map[q] = it->second;
     }
-    const std::vector<u32> src = sssp_sources(strategy, uq);
-    std::unordered_set<u32> distinct(src.begin(), src.end());
-    for (u64 q = 0; q < k; ++q) src_out[q] = (map[q] == NONE) ? NONE : src[map[q]];
+    const std::vector<SrcDir> src = sssp_sources(strategy, directed, uq);
+    std::unordered_set<u64> distinct;
+    for (const SrcDir& x : src) distinct.insert(((u64)x.v << 1) | x.dir);
+    for (u64 q = 0; q < k; ++q) {
+        src_out[q] = (map[q] == NONE) ? NONE : src[map[q]].v;
+        if (dir_out) dir_out[q] = (map[q] == NONE) ? 0u : src[map[q]].dir;
+    }
     *n_sources = distinct.size();
     return PPSP_OK;
 }

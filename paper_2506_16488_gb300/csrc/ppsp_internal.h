@@ -42,6 +42,8 @@ enum : u32 { ERRB_TIMEOUT = 1u, ERRB_OVERFLOW = 2u, ERRB_INTERNAL = 4u };
 struct GraphDev {
     const u32* off;       // [n+1]
     const uint2* edges;   // [m] (target, weight)
+    const u32* off_t;     // [n+1] transpose (in-edges); the same arrays as off / edges when undirected
+    const uint2* edges_t; // [m] (source, weight)
     const int2* pc;       // [n] integer potential coordinates, or null
     u32 n;
     u32 pot_shift;        // F: h = isqrt(d2 >> 2F)
@@ -52,6 +54,8 @@ struct SearchDev {
     u32 pbeg, pcnt;       // partners[pbeg .. pbeg+pcnt)
     u32 pot;              // 1: bidirectional A* potential rho_i(v) = h_{pot_b}(v) - h_{src}(v)
     u32 pot_b;            // partner vertex of the potential
+    u32 dir;              // 0: searches out-edges (from a source); 1: in-edges (back from a target)
+    u32 pad;
     i64 key_off;          // added to keys so the source's key is 0
 };
 

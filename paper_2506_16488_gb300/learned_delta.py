@@ -34,12 +34,14 @@ def weights_path(mode: str) -> str:
 
 
 def sweep(G: ppsp.Graph, pairs: np.ndarray, mode: str, grid=GRID, stream=None, reps: int = 1,
-          patience: int = 2, **opts):
+          patience: int = 2, start: int = 0, **opts):
     """Time every group of the batch for Delta = Delta_default * 2^j.
 
-    Like the paper's doubling search (Sec. 6.1) the sweep starts at j = 0 and
-    walks down, then up, while the batch's total time improves (stopping after
-    `patience` worse points).  Grid points it never visits get time +inf.
+    Like the paper's doubling search (Sec. 6.1) the sweep starts at j = start
+    (0: the default increment; large graphs start lower, where the default is
+    far too coarse and slow to time) and walks down, then up, while the
+    batch's total time improves (stopping after `patience` worse points).
+    Grid points it never visits get time +inf.
     Returns (features [groups, 12], times_ns [groups, len(grid)], default_delta).
     """
     import torch
@@ -71,8 +73,8 @@ def sweep(G: ppsp.Graph, pairs: np.ndarray, mode: str, grid=GRID, stream=None, r
         cols[j] = best
         return best.sum()
 
-    j0 = grid.index(0)
-    best_total = run(0)
+    j0 = grid.index(start)
+    best_total = run(start)
     for direction in (-1, 1):
         worse, k = 0, j0 + direction
         while 0 <= k < len(grid) and worse < patience:
@@ -91,8 +93,15 @@ def sweep(G: ppsp.Graph, pairs: np.ndarray, mode: str, grid=GRID, stream=None, r
     return state["feats"], times, default
 
 
-def labels_from_times(times: np.ndarray, grid=GRID) -> np.ndarray:
-    return np.asarray(grid, dtype=np.float32)[np.argmin(times, axis=1)]
+def labels_from_times(times: np.ndarray, grid=GRID, tie: float = 0.05) -> np.ndarray:
+    """Label of each group: the smallest grid point whose time is within
+    `tie` of the group's best.  Time grows slowly as Delta shrinks below the
+    best and steeply (many more re-extractions) as it grows above it, so a
+    near-tie is broken towards the smaller increment."""
+    best = times.min(axis=1, keepdims=True)
+    ok = times <= best * (1.0 + tie)
+    first = np.argmax(ok, axis=1)  # grid is increasing: the first True is the smallest Delta
+    return np.asarray(grid, dtype=np.float32)[first]
 
 
 def regret(times: np.ndarray, y_pred: np.ndarray, grid=GRID) -> float:
@@ -105,8 +114,11 @@ def regret(times: np.ndarray, y_pred: np.ndarray, grid=GRID) -> float:
     return float(chosen / times.min(axis=1).sum() - 1.0)
 
 
-def default_regret(times: np.ndarray, grid=GRID) -> float:
+def default_regret(times: np.ndarray, grid=GRID):
+    """Regret of the default increment, or None when the sweep never timed it."""
     j0 = list(grid).index(0)
+    if not np.isfinite(times[:, j0]).all():
+        return None
     return float(times[:, j0].sum() / times.min(axis=1).sum() - 1.0)
 
 
@@ -154,36 +166,80 @@ def load_model(mode: str, directory: str = WEIGHTS_DIR):
     return ppsp.DeltaModel(p)
 
 
-def _training_sets(mode: str):
-    """Query sets used for training: held-out seeds, several graph shapes."""
+def _training_sets(mode: str, build: bool = True):
+    """Query sets used for training: held-out seeds, several graph shapes.
+    With build=False only the names and sweep starts are returned (graphs and
+    pairs None), for training from stored sweeps."""
     from workloads import near_mid_far_pairs, random_pairs, rmat_graph, road_like_graph, grid_graph, clique_pairs
 
+    if not build:
+        names = [("road1024", 0), ("road512", 0), ("grid64", 0), ("road2048", -3), ("road4096", -4)]
+        if mode == "bids":
+            names.append(("rmat18", 0))
+        return [(n, None, None, st) for n, st in names]
+    # (name, graph, pairs, first grid point of the sweep)
     sets = []
     g = road_like_graph(1024, seed=2001)  # the road-like benchmark graph, other queries
     p, _ = near_mid_far_pairs(g, 1000, seed=2777)
-    sets.append(("road1024", g, p))
+    sets.append(("road1024", g, p, 0))
     g = road_like_graph(512, seed=9001)
     p, _ = near_mid_far_pairs(g, 600, seed=9002)
-    sets.append(("road512", g, np.concatenate([p, clique_pairs(g, 12, 9003)])))
+    sets.append(("road512", g, np.concatenate([p, clique_pairs(g, 12, 9003)]), 0))
     g = grid_graph(64, seed=9101)
-    sets.append(("grid64", g, random_pairs(g, 300, 9102)))
+    sets.append(("grid64", g, random_pairs(g, 300, 9102), 0))
+    # larger road-like graphs (other seeds than the benchmark and serving
+    # graphs): the increment that works shrinks with graph size
+    g = road_like_graph(2048, seed=9401)
+    p, _ = near_mid_far_pairs(g, 300, seed=9402)
+    sets.append(("road2048", g, p, -3))
+    g = road_like_graph(4096, seed=9501)
+    p, _ = near_mid_far_pairs(g, 120, seed=9502)
+    sets.append(("road4096", g, p, -4))
     if mode == "bids":
         g = rmat_graph(18, seed=9201)
-        sets.append(("rmat18", g, random_pairs(g, 128, 9202)))
+        sets.append(("rmat18", g, random_pairs(g, 128, 9202), 0))
     return sets
 
 
-def build_and_train(mode: str, out_dir: str = WEIGHTS_DIR, epochs: int = 600, log=print) -> dict:
-    """Sweep Delta on the training sets, train, report regret, save weights."""
-    feats_all, labels_all, meta_sets = [], [], []
+def ceil_regret(times: np.ndarray, y_pred: np.ndarray, grid=GRID) -> float:
+    """Like `regret`, but a prediction between two grid points is charged the
+    time of the larger increment (the pessimistic side of the steep curve)."""
+    ok = _finite_cols(times)
+    g = np.asarray(grid, dtype=np.float64)[ok]
+    times = times[:, ok]
+    idx = np.searchsorted(g, np.clip(y_pred, g[0], g[-1]) - 1e-6)
+    chosen = times[np.arange(times.shape[0]), np.minimum(idx, g.shape[0] - 1)].sum()
+    return float(chosen / times.min(axis=1).sum() - 1.0)
+
+
+MARGINS = tuple(np.arange(0.0, 1.51, 0.25))
+
+
+def build_and_train(mode: str, out_dir: str = WEIGHTS_DIR, epochs: int = 600, log=print,
+                    sweeps_dir: str | None = None, evaluate_sets: bool = True) -> dict:
+    """Sweep Delta on the training sets (or load earlier sweeps from
+    `sweeps_dir`), train, pick a safety margin, report regret, save weights.
+
+    The margin m is subtracted from every prediction (folded into the output
+    bias): the smallest m in MARGINS that minimises the summed pessimistic
+    regret (`ceil_regret`) over the training sets."""
+    feats_all, labels_all, times_all, meta_sets = [], [], [], []
     t0 = time.time()
-    for name, g, pairs in _training_sets(mode):
-        with ppsp.Graph.from_csr(g, with_coords=g.coords is not None) as G:
-            m = mode if (mode != "bidastar" or g.coords is not None) else "bids"
-            feats, times, default = sweep(G, pairs, m)
+    os.makedirs(out_dir, exist_ok=True)
+    for name, g, pairs, start in _training_sets(mode, build=sweeps_dir is None):
+        if sweeps_dir is not None:
+            d = np.load(os.path.join(sweeps_dir, f"sweep_{mode}_{name}.npz"))
+            feats, times, default = d["feats"], d["times"], int(d["default"])
+        else:
+            with ppsp.Graph.from_csr(g, with_coords=g.coords is not None) as G:
+                m = mode if (mode != "bidastar" or g.coords is not None) else "bids"
+                feats, times, default = sweep(G, pairs, m, start=start)
         lab = labels_from_times(times)
+        np.savez_compressed(os.path.join(out_dir, f"sweep_{mode}_{name}.npz"), feats=feats, times=times,
+                            default=default)
         feats_all.append(feats)
         labels_all.append(lab)
+        times_all.append(times)
         meta_sets.append({"set": name, "groups": int(feats.shape[0]), "default_delta": default,
                           "default_regret": default_regret(times),
                           "swept": [j for j, ok in zip(GRID, _finite_cols(times)) if ok],
@@ -193,14 +249,32 @@ def build_and_train(mode: str, out_dir: str = WEIGHTS_DIR, epochs: int = 600, lo
     Y = np.concatenate(labels_all)
     model, loss = train(F, Y, epochs=epochs)
     pred = model.predict(F)
+    # safety margin against the steep side of the time curve
+    offs = np.cumsum([0] + [f.shape[0] for f in feats_all])
+    scores = []
+    for mg in MARGINS:
+        scores.append(sum(ceil_regret(t, pred[offs[i]:offs[i + 1]] - mg) for i, t in enumerate(times_all)))
+    margin = float(MARGINS[int(np.argmin(scores))])
+    if margin:
+        params = model.params()
+        params[-1] -= margin  # output bias b3
+        model.close()
+        model = ppsp.DeltaModel(params)
+    for i, t in enumerate(times_all):
+        meta_sets[i]["regret_learned"] = regret(t, pred[offs[i]:offs[i + 1]] - margin)
+        meta_sets[i]["ceil_regret_learned"] = ceil_regret(t, pred[offs[i]:offs[i + 1]] - margin)
     meta = {"mode": mode, "grid": list(GRID), "epochs": epochs, "train_loss": loss,
             "train_groups": int(F.shape[0]), "sets": meta_sets, "seconds": time.time() - t0,
             "features": "log2(1 + raw): h(s,t), deg(s), deg(t), w mean/std/min/max, n, m, |V_q|, |E_q|, "
                         "mean query-graph degree",
+            "label_rule": "smallest grid point within 5% of the group's best time",
+            "margin": margin, "margin_scores": {str(float(m)): float(v) for m, v in zip(MARGINS, scores)},
             "train_mae": float(np.abs(pred - Y).mean())}
-    meta["eval"] = evaluate(mode, log=log, model=model)
+    if evaluate_sets:
+        meta["eval"] = evaluate(mode, log=log, model=model)
+        meta["eval_large"] = evaluate_large(mode, log=log, model=model)
     path = save(model, mode, meta, out_dir)
-    log(json.dumps({"saved": path, "train_loss": loss, "train_mae": meta["train_mae"]}))
+    log(json.dumps({"saved": path, "train_loss": loss, "train_mae": meta["train_mae"], "margin": margin}))
     model.close()
     return meta
 
@@ -224,6 +298,30 @@ def evaluate(mode: str, log=print, model=None) -> dict:
     res = {"mode": mode, "eval_set": "road1024 near/mid/far (bench queries)", "groups": int(feats.shape[0]),
            "regret_learned": regret(times, y), "regret_default": default_regret(times),
            "best_grid_hist": {str(j): int((lab == j).sum()) for j in GRID if (lab == j).any()},
+           "pred_mean": float(y.mean())}
+    if own:
+        model.close()
+    log(json.dumps(res))
+    return res
+
+
+def evaluate_large(mode: str, log=print, model=None, k: int = 96) -> dict:
+    """Regret on k random queries of the 4096^2 road-like serving graph (its own
+    seed; training used other graphs of that size)."""
+    from workloads import config_workload, random_pairs
+
+    g = config_workload(5)["graph"]
+    pairs = random_pairs(g, k, 5501)
+    own = model is None
+    if own:
+        model = load_model(mode)
+    if model is None:
+        raise FileNotFoundError(weights_path(mode))
+    with ppsp.Graph.from_csr(g) as G:
+        feats, times, default = sweep(G, pairs, mode, start=-4)
+    y = model.predict(feats)
+    res = {"mode": mode, "eval_set": f"road4096 serving graph, {k} random pairs", "groups": int(feats.shape[0]),
+           "regret_learned": regret(times, y), "regret_default": default_regret(times),
            "pred_mean": float(y.mean())}
     if own:
         model.close()

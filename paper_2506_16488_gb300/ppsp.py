@@ -131,7 +131,7 @@ def load(build_if_missing: bool = False):
             "ppsp_plan_features": (S, [p, p, u64, p]),
             "ppsp_plan_group_times": (S, [p, p, u64, p]),
             "ppsp_plan_uses_graph": (S, [p, p]),
-            "ppsp_batch_sources": (S, [p, u64, i32, p, p]),
+            "ppsp_batch_sources": (S, [p, u64, i32, u32, p, p, p]),
             "ppsp_delta_model_create": (S, [p, p]),
             "ppsp_delta_model_destroy": (None, [p]),
             "ppsp_delta_model_get_params": (S, [p, p]),
@@ -161,17 +161,23 @@ def _ptr(a: Optional[np.ndarray]):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-def batch_sources(pairs, strategy: str | int = "vc") -> tuple:
+def batch_sources(pairs, strategy: str | int = "vc", undirected: bool = True, return_dirs: bool = False):
     """Sources of an SSSP-based batch (Sec. 4.3), computed on the host:
     (per-pair source vertex, 0xFFFFFFFF where s == t; number of distinct
-    sources).  strategy "sssp" = each query's own source, "vc" = an endpoint in
-    a vertex cover of the query graph."""
+    searches) and, with return_dirs, each pair's search direction (1 =
+    backward from its target over in-edges).  strategy "sssp" = each query's
+    own source, "vc" = an endpoint in a vertex cover of the query graph
+    (bipartite and minimum on a directed graph)."""
     pa = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
     k = pa.shape[0]
     out = np.zeros(max(1, k), dtype=np.uint32)
+    dirs = np.zeros(max(1, k), dtype=np.uint32)
     n = ctypes.c_uint64(0)
     st = STRATEGY[strategy] if isinstance(strategy, str) else int(strategy)
-    _check(load().ppsp_batch_sources(_ptr(pa), k, st, _ptr(out), ctypes.byref(n)), "ppsp_batch_sources")
+    _check(load().ppsp_batch_sources(_ptr(pa), k, st, UNDIRECTED if undirected else 0, _ptr(out), _ptr(dirs),
+                                     ctypes.byref(n)), "ppsp_batch_sources")
+    if return_dirs:
+        return out[:k], int(n.value), dirs[:k]
     return out[:k], int(n.value)
 
 

@@ -139,6 +139,62 @@ def test_duplicates_reversed_and_self_pairs():
     assert ppsp.batch_sources(np.zeros((0, 2), np.uint32), "vc")[1] == 0
 
 
+def brute_min_bipartite_cover(pairs):
+    # nodes: (vertex, 0) for a source, (vertex, 1) for a target
+    nodes = sorted({(int(s), 0) for s, t in pairs if s != t} | {(int(t), 1) for s, t in pairs if s != t})
+    idx = {x: k for k, x in enumerate(nodes)}
+    edges = [(1 << idx[(int(s), 0)]) | (1 << idx[(int(t), 1)]) for s, t in pairs if s != t]
+    for r in range(len(nodes) + 1):
+        for sub in itertools.combinations(range(len(nodes)), r):
+            m = sum(1 << k for k in sub)
+            if all(e & m for e in edges):
+                return r
+    return len(nodes)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_directed_cover_is_minimum(seed):
+    # directed G_q is bipartite (sources, targets): the cover is minimum
+    # (Konig), every query is answered forward from its source or backward
+    # from its target
+    rng = np.random.default_rng(100 + seed)
+    nv = int(rng.integers(2, 9))
+    ne = int(rng.integers(1, 2 * nv + 1))
+    ids = rng.choice(10 ** 6, size=nv, replace=False).astype(np.uint32)
+    pairs = ids[rng.integers(0, nv, size=(ne, 2))]
+    src, n, dirs = ppsp.batch_sources(pairs, "vc", undirected=False, return_dirs=True)
+    for (s, t), x, d in zip(pairs, src, dirs):
+        if s == t:
+            assert x == NONE
+        else:
+            assert (x, d) in ((s, 0), (t, 1))
+    assert n == brute_min_bipartite_cover(pairs)
+    assert n == len({(int(x), int(d)) for x, d in zip(src, dirs) if x != NONE})
+
+
+def test_directed_cover_equals_maximum_matching():
+    # Konig: a minimum bipartite cover has the size of a maximum matching
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import maximum_bipartite_matching
+
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        pairs = rng.integers(0, 300, size=(2000, 2)).astype(np.uint32)
+        pairs = pairs[pairs[:, 0] != pairs[:, 1]]
+        _, n = ppsp.batch_sources(pairs, "vc", undirected=False)
+        uniq = np.unique(pairs, axis=0)
+        a = csr_matrix((np.ones(uniq.shape[0]), (uniq[:, 0], uniq[:, 1])), shape=(300, 300))
+        match = maximum_bipartite_matching(a, perm_type="column")
+        assert n == int((match >= 0).sum())
+    # a reversed star is one backward search from its centre
+    rs = np.array([(x, 5) for x in range(10, 40)], dtype=np.uint32)
+    src, n, dirs = ppsp.batch_sources(rs, "vc", undirected=False, return_dirs=True)
+    assert n == 1 and set(src.tolist()) == {5} and set(dirs.tolist()) == {1}
+    # (a, b) and (b, a) are two queries on a directed graph, one undirected
+    assert ppsp.batch_sources(np.array([(1, 2), (2, 1)]), "vc", undirected=False)[1] == 2
+    assert ppsp.batch_sources(np.array([(1, 2), (2, 1)]), "vc")[1] == 1
+
+
 def test_invalid_strategy():
     with pytest.raises(ppsp.PPSPError):
         ppsp.batch_sources(np.array([[0, 1]]), "multi")

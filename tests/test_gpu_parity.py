@@ -179,8 +179,10 @@ def test_edge_cases():
         assert G.query_status(0, 1, mode="astar")[0] == ppsp.ERR_NO_COORDS
         assert G.query(0, 1, mode="bids") == 5
     with ppsp.Graph(off, tgt, w, None, undirected=False) as G:
-        assert G.query_status(0, 1, mode="bids")[0] == ppsp.ERR_UNSUPPORTED
+        # a directed graph searches backward from t over its transpose
+        assert G.query(0, 1, mode="bids") == 5
         assert G.query(0, 2, mode="et") == 12
+        assert G.query(0, 4, mode="bids") == INF
     one = np.zeros(2, dtype=np.uint64)
     with ppsp.Graph(one, np.zeros(0, np.uint32), np.zeros(0, np.uint32)) as G:
         assert G.query(0, 0) == 0

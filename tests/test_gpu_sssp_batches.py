@@ -86,7 +86,8 @@ def test_u64_and_disconnected():
 
 
 def test_directed_graph():
-    # Plain-SSSP follows out-edges from each source; VC needs an undirected graph
+    # Plain-SSSP follows out-edges from each source; VC-SSSP covers the
+    # bipartite query graph, a target in the cover searching in-edges
     off = np.array([0, 1, 2, 3, 3], dtype=np.uint64)
     tgt = np.array([1, 2, 3], dtype=np.uint32)
     w = np.array([4, 5, 6], dtype=np.uint32)
@@ -94,7 +95,9 @@ def test_directed_graph():
     want = oracle.pairs(off, tgt, w, pairs)
     with ppsp.Graph(off, tgt, w, undirected=False) as G:
         assert np.array_equal(G.batch(pairs, mode="et", strategy="sssp"), want)
-        assert G.batch_status(pairs, mode="et", strategy="vc")[0] == ppsp.ERR_UNSUPPORTED
+        got, cnt = G.batch(pairs, mode="et", strategy="vc", return_counters=True)
+        assert np.array_equal(got, want)
+        assert cnt["searches"] == ppsp.batch_sources(pairs, "vc", undirected=False)[1]
 
 
 def test_paths_unsupported(road):

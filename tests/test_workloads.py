@@ -61,3 +61,21 @@ def test_config_workloads_small():
             assert pairs.ndim == 2 and pairs.shape[1] == 2
             assert pairs.max() < wl["graph"].n
     assert config_workload(4, small=True)["batches"]["mixed"].shape == (2048, 2)
+
+
+def test_one_way_graph_keeps_one_direction_of_every_edge():
+    from workloads import one_way_graph, road_like_graph
+
+    g = road_like_graph(40, seed=3)
+    d = one_way_graph(g, 0.3, 4)
+    und = {(int(u), int(v)): int(w) for u, v, w in zip(np.repeat(np.arange(g.n), np.diff(g.offsets).astype(np.int64)),
+                                                        g.targets, g.weights)}
+    dire = {(int(u), int(v)): int(w) for u, v, w in zip(np.repeat(np.arange(d.n), np.diff(d.offsets).astype(np.int64)),
+                                                         d.targets, d.weights)}
+    assert set(dire) <= set(und) and all(dire[e] == und[e] for e in dire)
+    pairs = {(min(u, v), max(u, v)) for u, v in und}
+    for a, b in pairs:
+        assert (a, b) in dire or (b, a) in dire  # never both directions dropped
+    one_way = sum(1 for a, b in pairs if ((a, b) in dire) != ((b, a) in dire))
+    assert abs(one_way / len(pairs) - 0.3) < 0.05
+    assert d.meta["directed"]

@@ -13,7 +13,7 @@ integer weights drawn uniformly at random as the paper does for graphs that
 come without weights.
 """
 
-from .graphs import CSRGraph, grid_graph, road_like_graph, rmat_graph, csr_from_undirected
+from .graphs import CSRGraph, grid_graph, road_like_graph, rmat_graph, csr_from_undirected, one_way_graph
 from .queries import (
     random_pairs,
     near_mid_far_pairs,
@@ -28,6 +28,7 @@ __all__ = [
     "road_like_graph",
     "rmat_graph",
     "csr_from_undirected",
+    "one_way_graph",
     "random_pairs",
     "near_mid_far_pairs",
     "star_pairs",

@@ -244,3 +244,30 @@ def rmat_graph(scale: int, seed: int, edge_factor: int = 16, a: float = 0.57, b:
     meta = {"kind": "rmat", "scale": scale, "edge_factor": edge_factor, "a": a, "b": b, "c": c,
             "seed": seed, "wmin": wmin, "wmax": wmax}
     return _finish(n, u, v, w, None, None, f"rmat{scale}", meta, keep_lcc=False)
+
+
+def one_way_graph(g: CSRGraph, frac: float, seed: int) -> CSRGraph:
+    """Directed variant of an undirected graph: for a seeded fraction of its
+    undirected edges one direction (chosen at random) is dropped, the rest keep
+    both (one-way streets on a road-like graph).  Coordinates are kept; the
+    result is a directed CSR (rows sorted by target), ``meta["directed"]``."""
+    rng = np.random.default_rng(seed)
+    deg = np.diff(g.offsets).astype(np.int64)
+    src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    dst = g.targets.astype(np.int64)
+    lo, hi = np.minimum(src, dst), np.maximum(src, dst)
+    # one decision per undirected edge {lo, hi}: keep both, or only lo->hi / hi->lo
+    key = lo * g.n + hi
+    uniq, inv = np.unique(key, return_inverse=True)
+    drop = rng.random(uniq.shape[0]) < frac
+    keep_fwd = rng.random(uniq.shape[0]) < 0.5  # if dropping: keep lo->hi, else hi->lo
+    d, kf = drop[inv], keep_fwd[inv]
+    is_fwd = src == lo
+    keep = ~d | (kf & is_fwd) | (~kf & ~is_fwd)
+    src, dst, w = src[keep], dst[keep], g.weights[keep]
+    off = np.zeros(g.n + 1, dtype=np.uint64)
+    np.cumsum(np.bincount(src, minlength=g.n), out=off[1:])
+    meta = dict(g.meta)
+    meta.update({"directed": True, "one_way_frac": frac, "one_way_seed": seed})
+    return CSRGraph(n=g.n, offsets=off, targets=dst.astype(np.uint32), weights=w.astype(np.uint32),
+                    coords=g.coords, grid_xy=g.grid_xy, lcc=g.lcc, name=g.name + f"-oneway{frac}", meta=meta)
