@@ -527,7 +527,7 @@ def main():
     ap.add_argument("--queries", type=int, default=0, help="strided subset of the batch (profiling)")
     ap.add_argument("--plain-queries", type=int, default=200,
                     help="plain baseline: strided subset of the batch, answered one at a time")
-    ap.add_argument("--plain-teams", type=int, nargs="*", default=[16, 64, 0],
+    ap.add_argument("--plain-teams", type=int, nargs="*", default=[1, 16, 64, 0],
                     help="team sizes tried for the plain one-query-at-a-time baseline (0 = all CTAs)")
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on resident CTAs (profiling)")
     ap.add_argument("--compare", nargs="*", default=[], choices=["plain_star", "sssp", "vc", "auto"],

@@ -92,7 +92,9 @@ enum {
                                   search from its centre and any other component as
                                   independent pairs (Plain*); without potentials a
                                   component with a vertex cover of at most a quarter of
-                                  its vertices runs as VC-SSSP, any other as Multi-BiDS.
+                                  its vertices runs as VC-SSSP, any other as Multi-BiDS,
+                                  except on graphs of average degree >= 8 (the social
+                                  shape), where every component runs as VC-SSSP.
                                   ET / A*: sources with 4 or more targets run one
                                   multi-target search                                   */
 };

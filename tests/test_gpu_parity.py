@@ -356,3 +356,20 @@ def test_stepping_rho_road_far_list_and_spills(rho):
                 got = G.batch(pairs, mode="bidastar", strategy=strategy, team_ctas=1, big_team_ctas=1,
                               stepping_rho=rho, delta=delta)
                 assert np.array_equal(got, want), (delta, strategy)
+
+
+def test_large_clique_uncached_partners_and_split():
+    # a 50-clique has 2,450 partner entries (more than the shared-memory
+    # partner cache holds) and a 70-clique more vertices than one Multi-BiDS
+    # group takes (it is split into sub-groups)
+    g = road_like_graph(72, seed=97)
+    for size in (50, 70):
+        pairs = clique_pairs(g, size, 98 + size)
+        want = oracle.pairs(g.offsets, g.targets, g.weights, pairs)
+        with ppsp.Graph.from_csr(g) as G:
+            for team in (1, 4):
+                got, cnt = G.batch(pairs, mode="bids", strategy="multi", big_team_ctas=team, team_ctas=team,
+                                   return_counters=True)
+                assert np.array_equal(got, want), (size, team)
+            if size == 70:
+                assert cnt["groups"] > 1

@@ -175,3 +175,18 @@ def test_auto_strategy_choices():
         assert st == ppsp.OK and np.array_equal(dist, oracle.pairs(g.offsets, g.targets, g.weights, star))
         for (s, t), p in zip(star, paths):
             assert p is not None and p[0] == s and p[-1] == t
+
+
+def test_auto_strategy_on_a_dense_graph():
+    # average degree >= 8 (the social shape): every component, isolated pairs
+    # too, runs as VC-SSSP single-source searches
+    from workloads import rmat_graph
+
+    g = rmat_graph(12, seed=93)
+    assert g.m >= 8 * g.n
+    pairs = np.concatenate([random_pairs(g, 20, 94), star_pairs(g, 10, 95), clique_pairs(g, 5, 96)])
+    want = oracle.pairs(g.offsets, g.targets, g.weights, pairs)
+    with ppsp.Graph.from_csr(g, with_coords=False) as G:
+        got, cnt = G.batch(pairs, mode="bids", strategy="auto", return_counters=True)
+        assert np.array_equal(got, want)
+        assert cnt["searches"] == ppsp.batch_sources(pairs, "vc")[1]
