@@ -113,7 +113,8 @@ typedef struct {
     int32_t frontier;        /* PPSP_FRONTIER_* (default AUTO)                              */
     int32_t layout;          /* PPSP_LAYOUT_* (default AUTO)                                */
     int32_t batch_strategy;  /* PPSP_BATCH_* (default MULTI)                                */
-    int32_t block_threads;   /* 256, 512 or 1024 threads per CTA; 0 = auto                 */
+    int32_t block_threads;   /* 256, 512 or 1024 threads per CTA; 0 = auto: 1024 when every
+                                team is one CTA (the bucketed path), else 512              */
     int32_t team_ctas;       /* CTAs cooperating on one small group (pair); 0 = auto        */
     int32_t big_team_ctas;   /* CTAs cooperating on one multi-search group; 0 = auto        */
     uint32_t dense_den;      /* frontier goes dense above (searches * n) / dense_den; 0=auto */

@@ -665,12 +665,12 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
 // far list full sets its bit in the slot's spill bitmap and is recovered from
 // its current distance when nothing else is left.
 #ifndef PPSP_RING_CAP
-#define PPSP_RING_CAP 256
+#define PPSP_RING_CAP 64  // a small ring leaves more of the SM's L1 to the adjacency and offsets
 #endif
 template <typename D>
 struct LR {
     static constexpr u32 NB = LR_NB;                       // buckets in the ring
-    static constexpr u32 CAP = sizeof(D) == 4 ? PPSP_RING_CAP : PPSP_RING_CAP / 2;  // shared-memory entries per bucket
+    static constexpr u32 CAP = PPSP_RING_CAP;  // shared-memory entries per bucket
     static constexpr size_t bytes() { return (size_t)NB * CAP * (4 + sizeof(D)) + NB * 4; }
 };
 
@@ -904,7 +904,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
         // pair groups: RX edges per thread at a time, their loads and atomics
         // issued together (instruction-level parallelism on the dependent
         // edge -> distance -> atomicMin chain)
-        constexpr int RX = PPSP_RELAX_ILP;
+        constexpr int RX = (B >= 1024) ? 1 : PPSP_RELAX_ILP;  // 1,024 threads: 64 registers
         for (u32 e0 = t; e0 < total; e0 += RX * B) {
             u32 v2[RX], si[RX], f2[RX];
             u64 nd[RX], own[RX], oth[RX], old[RX];
