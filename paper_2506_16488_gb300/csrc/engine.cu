@@ -1354,7 +1354,10 @@ __device__ bool find_paths(const EngineArgs& a, const TeamCtx& tc, GCtx<D>& c, S
 // ----------------------------------------------------------------------------
 // one group
 // ----------------------------------------------------------------------------
-template <typename D, int B>
+// LOCAL: every team is one CTA on the bucketed path (the host guarantees it),
+// so the queue / bitmap path is compiled out and the kernel needs fewer
+// registers.
+template <typename D, int B, bool LOCAL>
 __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev& slot, u32 gi,
                           Smem<B>& sm, u64* cnt_acc) {
     const u32 t = threadIdx.x;
@@ -1414,6 +1417,10 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
     // one-CTA teams keep the frontier in shared memory (run_local); the
     // policies SPARSE and DENSE force the global queue / bitmap path
     const bool local = (tc.size == 1) && (a.frontier == PPSP_FRONTIER_AUTO) && !tc.global_bar;
+    if (LOCAL && !local) {  // the host chose the local-only kernel for a plan it cannot run
+        if (t == 0) atomicOr(a.err, ERRB_INTERNAL);
+        return false;
+    }
     if (tc.rank == 0) {
         if (t < G.scnt) {
             const u32 f = flat_of(G, c.n, sm.src[t], t);
@@ -1499,7 +1506,7 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
         }
         __syncthreads();
     }
-    for (; !local; ++r) {
+    for (; !LOCAL && !local; ++r) {
         const u32 cur = r % 3, nxt = (r + 1) % 3, old = (r + 2) % 3;
         const u32 bcur = r & 1u, bnxt = bcur ^ 1u;
         if (t == 0) {
@@ -1695,12 +1702,13 @@ constexpr size_t engine_smem_bytes() {
 
 // Threads per SM the engine is compiled to keep resident (register budget):
 // 512 gives one 512-thread CTA per SM up to 128 registers per thread (the
-// four-way relaxation keeps its loads in registers instead of spilling).
+// two-way relaxation keeps its loads in registers instead of spilling); a
+// 1,024-thread CTA gets 64.
 #ifndef PPSP_ENGINE_SM_THREADS
 #define PPSP_ENGINE_SM_THREADS 512
 #endif
 
-template <typename D, int B>
+template <typename D, int B, bool LOCAL>
 __global__ void __launch_bounds__(B, (PPSP_ENGINE_SM_THREADS / B) > 0 ? (PPSP_ENGINE_SM_THREADS / B) : 1)
     engine_kernel(EngineArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1732,7 +1740,7 @@ __global__ void __launch_bounds__(B, (PPSP_ENGINE_SM_THREADS / B) > 0 ? (PPSP_EN
         const u32 gi = sm.group;
         if (!team_sync(tc, a, &sm.flag)) break;  // everyone has read ts->group
         if (gi == NONE) break;
-        if (!run_group<D, B>(a, tc, slot, gi, sm, acc)) break;
+        if (!run_group<D, B, LOCAL>(a, tc, slot, gi, sm, acc)) break;
     }
     // counters
     if (a.counters) {
@@ -1750,47 +1758,49 @@ __global__ void __launch_bounds__(B, (PPSP_ENGINE_SM_THREADS / B) > 0 ? (PPSP_EN
 // ----------------------------------------------------------------------------
 // host side
 // ----------------------------------------------------------------------------
-template <typename D, int B>
+template <typename D, int B, bool LOCAL>
 static ppsp_status set_smem_attr() {
     static bool done = false;  // per instantiation; the attribute is per device function
     if (!done) {
-        PPSP_CUDA_TRY(cudaFuncSetAttribute(engine_kernel<D, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        PPSP_CUDA_TRY(cudaFuncSetAttribute(engine_kernel<D, B, LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)engine_smem_bytes<D, B>()));
         done = true;
     }
     return PPSP_OK;
 }
 
-template <typename D, int B>
+template <typename D, int B, bool LOCAL>
 static ppsp_status launch_t(const EngineArgs& a, u32 grid, cudaStream_t stream) {
-    ppsp_status st = set_smem_attr<D, B>();
+    ppsp_status st = set_smem_attr<D, B, LOCAL>();
     if (st != PPSP_OK) return st;
     EngineArgs args = a;
     void* params[] = {&args};
-    PPSP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)engine_kernel<D, B>, dim3(grid), dim3(B),
+    PPSP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)engine_kernel<D, B, LOCAL>, dim3(grid), dim3(B),
                                               params, engine_smem_bytes<D, B>(), stream));
     return PPSP_OK;
 }
 
 ppsp_status launch_engine(const EngineArgs& a, int dist_bits, int block_threads, u32 grid,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, bool local_only) {
     if (dist_bits == 32) {
-        if (block_threads == 256) return launch_t<u32, 256>(a, grid, stream);
-        if (block_threads == 512) return launch_t<u32, 512>(a, grid, stream);
-        if (block_threads == 1024) return launch_t<u32, 1024>(a, grid, stream);
+        if (block_threads == 256) return launch_t<u32, 256, false>(a, grid, stream);
+        if (block_threads == 512) return launch_t<u32, 512, false>(a, grid, stream);
+        if (block_threads == 1024)
+            return local_only ? launch_t<u32, 1024, true>(a, grid, stream) : launch_t<u32, 1024, false>(a, grid, stream);
     } else {
-        if (block_threads == 256) return launch_t<u64, 256>(a, grid, stream);
-        if (block_threads == 512) return launch_t<u64, 512>(a, grid, stream);
-        if (block_threads == 1024) return launch_t<u64, 1024>(a, grid, stream);
+        if (block_threads == 256) return launch_t<u64, 256, false>(a, grid, stream);
+        if (block_threads == 512) return launch_t<u64, 512, false>(a, grid, stream);
+        if (block_threads == 1024)
+            return local_only ? launch_t<u64, 1024, true>(a, grid, stream) : launch_t<u64, 1024, false>(a, grid, stream);
     }
     return PPSP_ERR_INVALID_ARG;
 }
 
 template <typename D, int B>
 static ppsp_status occ_t(int* bpsm) {
-    ppsp_status st = set_smem_attr<D, B>();
+    ppsp_status st = set_smem_attr<D, B, false>();
     if (st != PPSP_OK) return st;
-    PPSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bpsm, engine_kernel<D, B>, B,
+    PPSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bpsm, engine_kernel<D, B, false>, B,
                                                                 engine_smem_bytes<D, B>()));
     return PPSP_OK;
 }

@@ -19,6 +19,7 @@ struct ppsp_plan {
     u64 k = 0;
     int dist_bits = 32;
     int block = 512;
+    bool local_only = false;           // every team is one CTA on the bucketed path
     u32 grid = 0;
     std::vector<GroupDev> groups;
     std::vector<SearchDev> searches;
@@ -765,8 +766,12 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         for (auto& tm : teams) all_single = all_single && tm.size == 1;
         int bpsm_big = 0, sms_big = 0;
         if (all_single && engine_occupancy(o.dist_bits, 1024, &bpsm_big, &sms_big) == PPSP_OK &&
-            (u64)bpsm_big * (u64)sms_big >= grid)
+            (u64)bpsm_big * (u64)sms_big >= grid) {
             P->block = 1024;
+            // the kernel without the queue / bitmap path (fewer registers);
+            // the barrier test hook needs the team barrier, so not with it
+            P->local_only = o.debug_flags == 0;
+        }
     }
 
     // ---- slots ----
@@ -992,7 +997,7 @@ static ppsp_status plan_launch_direct(ppsp_plan* P, u64* d_out) {
         if (st != PPSP_OK) return st;
     }
     if (!P->groups.empty()) {
-        st = launch_engine(P->args, P->dist_bits, P->block, P->grid, P->stream);
+        st = launch_engine(P->args, P->dist_bits, P->block, P->grid, P->stream, P->local_only);
         if (st != PPSP_OK) return st;
     }
     if (d_out) {

@@ -170,7 +170,7 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
 
 // Launch the persistent engine.  dist_bits selects the distance width.
 ppsp_status launch_engine(const EngineArgs& a, int dist_bits, int block_threads, u32 grid,
-                          cudaStream_t stream);
+                          cudaStream_t stream, bool local_only = false);
 
 // Max resident CTAs of the engine for a block size / distance width.
 ppsp_status engine_occupancy(int dist_bits, int block_threads, int* blocks_per_sm, int* sms);
