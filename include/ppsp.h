@@ -146,7 +146,9 @@ typedef struct {
 typedef struct {
     uint64_t extracted;   /* frontier entries taken and not pruned (X)           */
     uint64_t edges;       /* adjacency entries scanned (E)                        */
-    uint64_t relaxed;     /* successful WriteMin relaxations (R)                  */
+    uint64_t relaxed;     /* WriteMin relaxations that lowered a distance (R); on
+                             the one-CTA path: lower than the value read just
+                             before, a concurrent smaller write aside            */
     uint64_t pushed;      /* frontier insertions (P)                              */
     uint64_t rounds;      /* stepping rounds summed over groups                   */
     uint64_t groups;      /* searched groups (pairs or query-graph components)    */

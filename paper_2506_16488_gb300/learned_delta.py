@@ -1,4 +1,4 @@
-"""Learned stepping increment: sweep labels, train the MLP on the GPU, judge regret.
+"""Learned stepping increment: sweep labels, train the MLP on the GPU, measure regret.
 
 The paper picks Delta for Delta*-stepping by doubling it until the geometric
 mean time stops improving (Sec. 6.1).  Here the same sweep produces training

@@ -1,4 +1,4 @@
-"""Shortest paths returned with the distances (SURVEY K9).
+"""Shortest paths returned with the distances.
 
 Shortest paths need not be unique, so a returned path is checked for what is
 unique: it starts at s, ends at t, consecutive vertices are CSR neighbours,
