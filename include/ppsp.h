@@ -258,7 +258,11 @@ ppsp_status ppsp_batch(ppsp_graph* g, const uint32_t* pairs, uint64_t k, const p
  * d_dists_out captures the run's launches into a CUDA graph and every run
  * replays it (if the driver refuses the capture, runs launch directly).  A
  * plan keeps device memory until ppsp_plan_destroy and belongs to its graph.
- * Paths are not available through plans (use ppsp_batch).
+ * Its descriptor memory comes from the device's stream-ordered pool on
+ * opt->stream (creating or destroying a plan never synchronises other
+ * streams), so that stream must outlive the plan; ppsp_plan_destroy waits for
+ * the plan's own work on it.  Paths are not available through plans (use
+ * ppsp_batch).
  */
 ppsp_status ppsp_plan_create(ppsp_graph* g, const uint32_t* pairs, uint64_t k,
                              const ppsp_options* opt, ppsp_plan** out);
