@@ -198,3 +198,16 @@ def test_directed_cover_equals_maximum_matching():
 def test_invalid_strategy():
     with pytest.raises(ppsp.PPSPError):
         ppsp.batch_sources(np.array([[0, 1]]), "multi")
+
+
+def test_golden_query_graph_patterns():
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "query_graph_patterns.json")
+    with open(path) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        pairs = np.array(c["pairs"], dtype=np.uint32)
+        assert ppsp.batch_sources(pairs, "vc")[1] == c["vc_sources"], c["name"]
+        assert ppsp.batch_sources(pairs, "sssp")[1] == c["plain_sssp_sources"], c["name"]
