@@ -8,9 +8,10 @@
  * early termination (ET, Sec. 3.2), A* (Sec. 3.3), bidirectional search (BiDS,
  * Sec. 3.4, Theorem 3.3) and bidirectional A* (BiD-A*, Sec. 3.5, Theorem 3.4),
  * and batches of queries organised as a query graph (Sec. 4.1) and searched
- * with Multi-BiDS (Sec. 4.2).  All arithmetic on distances is integer, so
- * results are exact.  The paper defines no programming interface; names and
- * layouts here are this library's own.
+ * with Multi-BiDS (Sec. 4.2) or single-source searches from a vertex cover
+ * (Sec. 4.3), on undirected or directed graphs (Sec. 4.4).  All arithmetic on
+ * distances is integer, so results are exact.  The paper defines no
+ * programming interface; names and layouts here are this library's own.
  *
  * Conventions for every entry point:
  *  - Every function returns a ppsp_status; nothing aborts or throws across the
@@ -77,7 +78,8 @@ enum { PPSP_LAYOUT_AUTO = 0, PPSP_LAYOUT_INTERLEAVED = 1, PPSP_LAYOUT_STACKED = 
 enum {
     PPSP_BATCH_MULTI = 0,      /* Multi-BiDS: one search per query-graph vertex, shared  */
     PPSP_BATCH_PLAIN_STAR = 1, /* Plain*: every query its own pair of searches, all at once */
-    PPSP_BATCH_PLAIN = 2,      /* Plain: one query at a time, each on the whole GPU       */
+    PPSP_BATCH_PLAIN = 2,      /* Plain: one query at a time, each on one team of team_ctas
+                                  CTAs (default: the whole GPU)                           */
     PPSP_BATCH_SSSP = 3,       /* Plain-SSSP (Sec. 4.3): a single-source search from every
                                   query source; answers read from its distances          */
     PPSP_BATCH_VC = 4,         /* VC-SSSP (Sec. 4.3): single-source searches only from a
