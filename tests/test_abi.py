@@ -42,7 +42,9 @@ def test_options_defaults(lib):
     o = ppsp.Options()
     lib.ppsp_options_init(ctypes.byref(o))
     assert o.mode == 0 and o.dist_bits == 32 and o.delta == 0 and o.batch_strategy == 0
+    assert o.block_threads == 0 and o.stepping_rho == 0 and o.cuda_graph == 0 and o.want_paths == 0
     assert lib.ppsp_status_string(ppsp.ERR_TIMEOUT) == b"device wait timed out"
+
 
 
 def _create(lib, off, tgt, w, flags=1):
@@ -82,3 +84,33 @@ def test_null_handles_are_rejected(lib):
     assert lib.ppsp_plan_run(None, None) == ppsp.ERR_INVALID_ARG
     lib.ppsp_graph_destroy(None)
     lib.ppsp_plan_destroy(None)
+
+
+def test_python_structs_mirror_the_c_layout(tmp_path):
+    # sizes and field offsets of the option / counter / info structs as the C
+    # compiler lays them out from include/ppsp.h
+    import os
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "layout.c"
+    fields = [f for f, _ in ppsp.Options._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ppsp.h"', "int main(void) {",
+             '  printf("%zu %zu %zu\\n", sizeof(ppsp_options), sizeof(ppsp_counters), sizeof(ppsp_graph_info));']
+    for f in fields:
+        lines.append(f'  printf("%zu\\n", offsetof(ppsp_options, {f}));')
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    so, sc, si = (int(x) for x in out[:3])
+    assert so == ctypes.sizeof(ppsp.Options)
+    assert sc == ctypes.sizeof(ppsp.Counters)
+    assert si == ctypes.sizeof(ppsp.GraphInfo)
+    for f, off in zip(fields, out[3:]):
+        assert getattr(ppsp.Options, f).offset == int(off), f
