@@ -259,7 +259,9 @@ ppsp_status ppsp_batch(ppsp_graph* g, const uint32_t* pairs, uint64_t k, const p
  * opt->cuda_graph = 1 and a non-NULL stream, the first run for a given
  * d_dists_out captures the run's launches into a CUDA graph and every run
  * replays it (if the driver refuses the capture, runs launch directly).  A
- * plan keeps device memory until ppsp_plan_destroy and belongs to its graph.
+ * plan keeps device memory until ppsp_plan_destroy and belongs to its graph:
+ * destroy every plan of a graph before the graph (ppsp_plan_destroy takes the
+ * graph's lock).
  * Its descriptor memory comes from the device's stream-ordered pool on
  * opt->stream (creating or destroying a plan never synchronises other
  * streams), so that stream must outlive the plan; ppsp_plan_destroy waits for

@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 from typing import Optional
 
 import numpy as np
@@ -225,15 +226,22 @@ class Graph:
         self._h = h
         self.n = n
         self.m = int(tgt.shape[0])
+        self._plans = weakref.WeakSet()
+        self._models = {}
 
     @classmethod
     def from_csr(cls, g, undirected: bool = True, with_coords: bool = True):
         return cls(g.offsets, g.targets, g.weights, g.coords if with_coords else None, undirected)
 
     def close(self):
+        """Destroy the graph; its open plans are destroyed first (a plan
+        belongs to its graph and must not outlive it)."""
+        for p in list(getattr(self, "_plans", ())):
+            p.close()
         if getattr(self, "_h", None):
             load().ppsp_graph_destroy(self._h)
             self._h = None
+        self._models = {}
 
     def __del__(self):
         try:
@@ -247,16 +255,21 @@ class Graph:
     def __exit__(self, *exc):
         self.close()
 
+    def _handle(self):
+        if not getattr(self, "_h", None):
+            raise PPSPError(ERR_INVALID_ARG, "graph is closed")
+        return self._h
+
     def info(self) -> dict:
         gi = GraphInfo()
-        _check(load().ppsp_graph_get_info(self._h, ctypes.byref(gi)), "ppsp_graph_get_info")
+        _check(load().ppsp_graph_get_info(self._handle(), ctypes.byref(gi)), "ppsp_graph_get_info")
         return gi.as_dict()
 
     def query(self, s: int, t: int, **opts) -> int:
         o = make_options(**opts)
         d = ctypes.c_uint64(0)
         plen = ctypes.c_uint64(0)
-        st = load().ppsp_query(self._h, s, t, ctypes.byref(o), ctypes.byref(d), None, 0, ctypes.byref(plen))
+        st = load().ppsp_query(self._handle(), s, t, ctypes.byref(o), ctypes.byref(d), None, 0, ctypes.byref(plen))
         _check(st, "ppsp_query")
         return int(d.value)
 
@@ -264,7 +277,7 @@ class Graph:
         """(status, distance) without raising (for error-path tests)."""
         o = make_options(**opts)
         d = ctypes.c_uint64(0)
-        st = load().ppsp_query(self._h, s, t, ctypes.byref(o), ctypes.byref(d), None, 0, None)
+        st = load().ppsp_query(self._handle(), s, t, ctypes.byref(o), ctypes.byref(d), None, 0, None)
         return int(st), int(d.value)
 
     def batch(self, pairs, return_counters: bool = False, **opts):
@@ -273,7 +286,7 @@ class Graph:
         k = pa.shape[0]
         out = np.zeros(k, dtype=np.uint64)
         c = Counters()
-        st = load().ppsp_batch(self._h, _ptr(pa), k, ctypes.byref(o), _ptr(out), None, None, None,
+        st = load().ppsp_batch(self._handle(), _ptr(pa), k, ctypes.byref(o), _ptr(out), None, None, None,
                                ctypes.byref(c))
         _check(st, "ppsp_batch")
         return (out, c.as_dict()) if return_counters else out
@@ -284,7 +297,7 @@ class Graph:
         d = ctypes.c_uint64(0)
         plen = ctypes.c_uint64(0)
         buf = np.zeros(max(1, cap), dtype=np.uint32)
-        st = load().ppsp_query(self._h, s, t, ctypes.byref(o), ctypes.byref(d), _ptr(buf), cap, ctypes.byref(plen))
+        st = load().ppsp_query(self._handle(), s, t, ctypes.byref(o), ctypes.byref(d), _ptr(buf), cap, ctypes.byref(plen))
         n = int(plen.value)
         path = buf[:n].copy() if st == OK else None
         return int(st), int(d.value), path, n
@@ -300,7 +313,7 @@ class Graph:
         buf = np.zeros(max(1, int(off[-1])), dtype=np.uint32)
         out = np.zeros(k, dtype=np.uint64)
         lens = np.zeros(k, dtype=np.uint64)
-        st = load().ppsp_batch(self._h, _ptr(pa), k, ctypes.byref(o), _ptr(out), _ptr(buf), _ptr(off), _ptr(lens),
+        st = load().ppsp_batch(self._handle(), _ptr(pa), k, ctypes.byref(o), _ptr(out), _ptr(buf), _ptr(off), _ptr(lens),
                                None)
         paths = [buf[int(off[q]):int(off[q]) + int(lens[q])].copy() if lens[q] <= caps[q] else None
                  for q in range(k)]
@@ -310,7 +323,7 @@ class Graph:
         o = make_options(**opts)
         pa = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
         out = np.zeros(pa.shape[0], dtype=np.uint64)
-        st = load().ppsp_batch(self._h, _ptr(pa), pa.shape[0], ctypes.byref(o), _ptr(out), None, None,
+        st = load().ppsp_batch(self._handle(), _ptr(pa), pa.shape[0], ctypes.byref(o), _ptr(out), None, None,
                                None, None)
         return int(st), out
 
@@ -320,21 +333,21 @@ class Graph:
     def set_delta_model(self, mode: str | int, model: Optional["DeltaModel"]):
         """Plans of this mode with delta=0 use the model (kept alive by the graph)."""
         m = MODES[mode] if isinstance(mode, str) else int(mode)
-        _check(load().ppsp_graph_set_delta_model(self._h, m, model._h if model else None),
+        _check(load().ppsp_graph_set_delta_model(self._handle(), m, model._handle() if model else None),
                "ppsp_graph_set_delta_model")
-        if not hasattr(self, "_models"):
-            self._models = {}
         self._models[m] = model
+        if model is not None:
+            model._graphs.add(self)
 
     def potential_coords(self) -> np.ndarray:
         out = np.empty(2 * self.n, dtype=np.int64)
-        _check(load().ppsp_potential_coords(self._h, _ptr(out)), "ppsp_potential_coords")
+        _check(load().ppsp_potential_coords(self._handle(), _ptr(out)), "ppsp_potential_coords")
         return out.reshape(-1, 2)
 
     def potential_eval(self, anchor: int, vertices) -> np.ndarray:
         v = np.ascontiguousarray(vertices, dtype=np.uint32)
         out = np.empty(v.shape[0], dtype=np.int64)
-        _check(load().ppsp_potential_eval(self._h, anchor, _ptr(v), v.shape[0], _ptr(out)),
+        _check(load().ppsp_potential_eval(self._handle(), anchor, _ptr(v), v.shape[0], _ptr(out)),
                "ppsp_potential_eval")
         return out
 
@@ -348,37 +361,43 @@ class Plan:
         pa = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
         self.k = pa.shape[0]
         h = ctypes.c_void_p()
-        _check(load().ppsp_plan_create(graph._h, _ptr(pa), self.k, ctypes.byref(self._opts), ctypes.byref(h)),
-               "ppsp_plan_create")
+        _check(load().ppsp_plan_create(graph._handle(), _ptr(pa), self.k, ctypes.byref(self._opts),
+                                       ctypes.byref(h)), "ppsp_plan_create")
         self._h = h
+        graph._plans.add(self)
+
+    def _handle(self):
+        if not getattr(self, "_h", None):
+            raise PPSPError(ERR_INVALID_ARG, "plan is closed")
+        return self._h
 
     def run(self, d_out_ptr: int):
-        _check(load().ppsp_plan_run(self._h, ctypes.c_void_p(d_out_ptr)), "ppsp_plan_run")
+        _check(load().ppsp_plan_run(self._handle(), ctypes.c_void_p(d_out_ptr)), "ppsp_plan_run")
 
     def sync(self) -> dict:
         c = Counters()
-        _check(load().ppsp_plan_sync(self._h, ctypes.byref(c)), "ppsp_plan_sync")
+        _check(load().ppsp_plan_sync(self._handle(), ctypes.byref(c)), "ppsp_plan_sync")
         return c.as_dict()
 
     def features(self) -> np.ndarray:
         """Per-group model features, float32 [groups, 12]."""
         ng = ctypes.c_uint64(0)
-        _check(load().ppsp_plan_features(self._h, None, 0, ctypes.byref(ng)), "ppsp_plan_features")
+        _check(load().ppsp_plan_features(self._handle(), None, 0, ctypes.byref(ng)), "ppsp_plan_features")
         out = np.zeros((ng.value, MLP_FEATURES), dtype=np.float32)
-        _check(load().ppsp_plan_features(self._h, _ptr(out), ng.value, ctypes.byref(ng)), "ppsp_plan_features")
+        _check(load().ppsp_plan_features(self._handle(), _ptr(out), ng.value, ctypes.byref(ng)), "ppsp_plan_features")
         return out
 
     def uses_graph(self) -> bool:
         v = ctypes.c_int32(0)
-        _check(load().ppsp_plan_uses_graph(self._h, ctypes.byref(v)), "ppsp_plan_uses_graph")
+        _check(load().ppsp_plan_uses_graph(self._handle(), ctypes.byref(v)), "ppsp_plan_uses_graph")
         return bool(v.value)
 
     def group_times(self) -> np.ndarray:
         """Device ns per group of the last run, uint64 [groups]."""
         ng = ctypes.c_uint64(0)
-        _check(load().ppsp_plan_group_times(self._h, None, 0, ctypes.byref(ng)), "ppsp_plan_group_times")
+        _check(load().ppsp_plan_group_times(self._handle(), None, 0, ctypes.byref(ng)), "ppsp_plan_group_times")
         out = np.zeros(ng.value, dtype=np.uint64)
-        _check(load().ppsp_plan_group_times(self._h, _ptr(out), ng.value, ctypes.byref(ng)),
+        _check(load().ppsp_plan_group_times(self._handle(), _ptr(out), ng.value, ctypes.byref(ng)),
                "ppsp_plan_group_times")
         return out
 
@@ -393,26 +412,39 @@ class Plan:
         except Exception:
             pass
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
 
 class DeltaModel:
     """The stepping-increment MLP on the device (ppsp_delta_model_*)."""
 
     def __init__(self, params):
         p = np.ascontiguousarray(params, dtype=np.float32)
-        assert p.shape == (MLP_PARAMS,)
+        if p.shape != (MLP_PARAMS,):
+            raise ValueError(f"expected {MLP_PARAMS} parameters, got shape {p.shape}")
         h = ctypes.c_void_p()
         _check(load().ppsp_delta_model_create(_ptr(p), ctypes.byref(h)), "ppsp_delta_model_create")
         self._h = h
+        self._graphs = weakref.WeakSet()  # graphs that borrow this model
+
+    def _handle(self):
+        if not getattr(self, "_h", None):
+            raise PPSPError(ERR_INVALID_ARG, "model is closed")
+        return self._h
 
     def params(self) -> np.ndarray:
         out = np.empty(MLP_PARAMS, dtype=np.float32)
-        _check(load().ppsp_delta_model_get_params(self._h, _ptr(out)), "ppsp_delta_model_get_params")
+        _check(load().ppsp_delta_model_get_params(self._handle(), _ptr(out)), "ppsp_delta_model_get_params")
         return out
 
     def predict(self, feats) -> np.ndarray:
         f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MLP_FEATURES)
         out = np.empty(f.shape[0], dtype=np.float32)
-        _check(load().ppsp_delta_model_predict(self._h, _ptr(f), f.shape[0], _ptr(out)),
+        _check(load().ppsp_delta_model_predict(self._handle(), _ptr(f), f.shape[0], _ptr(out)),
                "ppsp_delta_model_predict")
         return out
 
@@ -421,7 +453,7 @@ class DeltaModel:
         y = np.ascontiguousarray(labels, dtype=np.float32)
         g = np.empty(MLP_PARAMS, dtype=np.float32)
         loss = ctypes.c_float(0)
-        _check(load().ppsp_delta_model_grad(self._h, _ptr(f), _ptr(y), f.shape[0], _ptr(g), ctypes.byref(loss)),
+        _check(load().ppsp_delta_model_grad(self._handle(), _ptr(f), _ptr(y), f.shape[0], _ptr(g), ctypes.byref(loss)),
                "ppsp_delta_model_grad")
         return g, float(loss.value)
 
@@ -429,14 +461,26 @@ class DeltaModel:
         f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MLP_FEATURES)
         y = np.ascontiguousarray(labels, dtype=np.float32)
         loss = ctypes.c_float(0)
-        _check(load().ppsp_delta_model_train(self._h, _ptr(f), _ptr(y), f.shape[0], epochs, lr,
+        _check(load().ppsp_delta_model_train(self._handle(), _ptr(f), _ptr(y), f.shape[0], epochs, lr,
                                              ctypes.byref(loss)), "ppsp_delta_model_train")
         return float(loss.value)
 
     def close(self):
+        """Destroy the model after detaching it from every open graph that
+        borrows it (graphs keep a pointer to it, not a copy)."""
+        for g in list(getattr(self, "_graphs", ())):
+            for mode, mm in list(g._models.items()):
+                if mm is self and getattr(g, "_h", None):
+                    g.set_delta_model(mode, None)
         if getattr(self, "_h", None):
             load().ppsp_delta_model_destroy(self._h)
             self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:
