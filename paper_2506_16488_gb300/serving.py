@@ -14,6 +14,12 @@ each result is the same alone and in the mix.
 
 The scheduling core (:class:`Scheduler`) has no GPU dependency; the executor
 (:class:`GpuExecutor`) runs plans through the C ABI.
+
+Request status: 0 answered; REJECTED (-1) can never fit one micro-batch or
+the memory budget; CANCELLED (-2) withdrawn by the client; a positive value
+is the library's ppsp_status for the micro-batch that carried it (for
+example PPSP_ERR_OOM when its plan could not get device memory); the loop
+goes on with the other requests.
 """
 
 from __future__ import annotations
@@ -24,6 +30,9 @@ from dataclasses import dataclass, field
 from typing import Callable, Optional
 
 import numpy as np
+
+REJECTED = -1
+CANCELLED = -2
 
 
 @dataclass
@@ -66,15 +75,27 @@ class Scheduler:
         self.free_lanes = list(range(lanes))
         self.in_use = 0
         self.rejected: list = []
+        self.cancelled: list = []
 
     def add(self, req: Request):
         need = self.bytes_for(req.pairs)
         if need > self.budget or req.pairs.shape[0] > self.max_pairs:
             # can never be admitted in one piece: refuse instead of waiting forever
-            req.status = -1
+            req.status = REJECTED
             self.rejected.append(req)
             return
         self.waiting.append(req)
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraw a waiting request; False if it is not waiting (not yet
+        added, already started or finished)."""
+        for req in self.waiting:
+            if req.rid == rid:
+                self.waiting.remove(req)
+                req.status = CANCELLED
+                self.cancelled.append(req)
+                return True
+        return False
 
     def next_batch(self) -> Optional[MicroBatch]:
         """Pack the oldest waiting requests that fit one lane and the memory budget."""
@@ -104,24 +125,60 @@ class Scheduler:
         self.free_lanes.sort()
 
 
-def serve(arrivals: list, executor, scheduler: Scheduler, clock=time.perf_counter, poll_s: float = 2e-4) -> dict:
+def serve(arrivals: list, executor, scheduler: Scheduler, clock=time.perf_counter, poll_s: float = 2e-4,
+          cancels=()) -> dict:
     """Run requests arriving at the given times (seconds from start).
 
-    arrivals: list of (t_arrival, pairs) sorted by time.  Returns per-request
-    results and latencies, p50/p99 and sustained queries/sec.
+    arrivals: list of (t_arrival, pairs) sorted by time; request ids are the
+    list positions.  cancels: (t, request id) sorted by time: a request that
+    has not started by then never runs; one already on the device completes
+    there (a running search is not interrupted) and its answer is dropped.
+    An executor error that carries a library status (``.status``) fails the
+    micro-batch's requests with that status; other exceptions propagate.
+    Returns per-request results and latencies, p50/p99 and sustained
+    queries/sec (over answered requests), and the rejected / cancelled /
+    failed counts.
     """
     reqs = [Request(i, np.ascontiguousarray(p, dtype=np.uint32).reshape(-1, 2), t) for i, (t, p) in
             enumerate(arrivals)]
     t0 = clock()
-    nxt = 0
+    nxt = nc = 0
     running: list = []
-    finished = 0
+    closed = 0  # requests that reached a final state
     total = len(reqs)
-    while finished + len(scheduler.rejected) < total:
+    withdrawn: set = set()  # cancelled before arrival, or while running
+
+    def close(mb, status, dists):
+        nonlocal closed
+        end = clock() - t0
+        off = 0
+        for r in mb.requests:
+            k = r.pairs.shape[0]
+            if r.rid in withdrawn:
+                r.status = CANCELLED
+            else:
+                r.result = None if dists is None else dists[off:off + k]
+                r.status = status
+                r.done = end
+            off += k
+        closed += len(mb.requests)
+        scheduler.finish(mb)
+
+    while closed + len(scheduler.rejected) + len(scheduler.cancelled) < total:
         now = clock() - t0
+        while nc < len(cancels) and cancels[nc][0] <= now:
+            rid = int(cancels[nc][1])
+            nc += 1
+            if not scheduler.cancel(rid) and 0 <= rid < total and reqs[rid].done is None:
+                withdrawn.add(rid)
         while nxt < total and reqs[nxt].arrival <= now:
-            scheduler.add(reqs[nxt])
+            r = reqs[nxt]
             nxt += 1
+            if r.rid in withdrawn:
+                r.status = CANCELLED
+                scheduler.cancelled.append(r)
+            else:
+                scheduler.add(r)
         while True:
             mb = scheduler.next_batch()
             if mb is None:
@@ -129,23 +186,20 @@ def serve(arrivals: list, executor, scheduler: Scheduler, clock=time.perf_counte
             for r in mb.requests:
                 r.start = clock() - t0
             mb.started = clock() - t0
-            mb.handle = executor.start(mb.pairs, mb.lane)
+            try:
+                mb.handle = executor.start(mb.pairs, mb.lane)
+            except Exception as e:
+                if not isinstance(getattr(e, "status", None), int):
+                    raise
+                close(mb, e.status, None)
+                continue
             running.append(mb)
         for mb in list(running):
             res = executor.poll(mb.handle)
             if res is None:
                 continue
             status, dists = res
-            end = clock() - t0
-            off = 0
-            for r in mb.requests:
-                k = r.pairs.shape[0]
-                r.result = dists[off:off + k]
-                r.status = status
-                r.done = end
-                off += k
-            finished += len(mb.requests)
-            scheduler.finish(mb)
+            close(mb, status, dists)
             running.remove(mb)
         if not running and nxt < total and not scheduler.waiting:
             # idle until the next arrival
@@ -154,9 +208,10 @@ def serve(arrivals: list, executor, scheduler: Scheduler, clock=time.perf_counte
                 time.sleep(min(wait, 0.01))
         else:
             time.sleep(poll_s)
-    span = max((r.done for r in reqs if r.done is not None), default=0.0)
-    lat = np.array([r.done - r.arrival for r in reqs if r.done is not None])
-    nq = sum(r.pairs.shape[0] for r in reqs if r.done is not None)
+    ok = [r for r in reqs if r.status == 0 and r.done is not None]
+    span = max((r.done for r in ok), default=0.0)
+    lat = np.array([r.done - r.arrival for r in ok])
+    nq = sum(r.pairs.shape[0] for r in ok)
     return {
         "requests": reqs,
         "latency_p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
@@ -165,6 +220,8 @@ def serve(arrivals: list, executor, scheduler: Scheduler, clock=time.perf_counte
         "span_s": float(span),
         "qps": float(nq / span) if span > 0 else None,
         "rejected": len(scheduler.rejected),
+        "cancelled": sum(r.status == CANCELLED for r in reqs),
+        "failed": sum(r.status > 0 for r in reqs),
     }
 
 
@@ -207,8 +264,12 @@ class GpuExecutor:
         s = self.streams[lane]
         plan = self.graph.plan(pairs, mode=self.mode, dist_bits=self.dist_bits, stream=s.cuda_stream,
                                max_ctas=self.lane_ctas, **self.opts)
-        out = self.torch.zeros(pairs.shape[0], dtype=self.torch.int64, device="cuda")
-        plan.run(out.data_ptr())
+        try:
+            out = self.torch.zeros(pairs.shape[0], dtype=self.torch.int64, device="cuda")
+            plan.run(out.data_ptr())
+        except BaseException:
+            plan.close()
+            raise
         ev = self.torch.cuda.Event()
         ev.record(s)
         return (plan, out, ev)

@@ -6,7 +6,8 @@ import time
 import numpy as np
 import pytest
 
-from paper_2506_16488_gb300.serving import Request, Scheduler, memory_model, poisson_arrivals, serve, slot_bytes
+from paper_2506_16488_gb300.serving import (CANCELLED, REJECTED, Request, Scheduler, memory_model, poisson_arrivals,
+                                            serve, slot_bytes)
 
 
 def _req(i, k, t=0.0):
@@ -68,6 +69,75 @@ def test_serve_loop_continuous_batching_with_fake_executor():
         assert np.array_equal(r.result, p[:, 0].astype(np.uint64) + p[:, 1])
         assert r.done >= r.arrival
     assert out["latency_p99_ms"] >= out["latency_p50_ms"] > 0
+
+
+def test_scheduler_cancel_withdraws_only_waiting_requests():
+    sch = Scheduler(lanes=1, max_pairs=4, budget=100, bytes_for=lambda p: p.shape[0])
+    for i in range(3):
+        sch.add(_req(i, 2))
+    a = sch.next_batch()  # requests 0 and 1 start
+    assert [r.rid for r in a.requests] == [0, 1]
+    assert not sch.cancel(0)  # already started
+    assert sch.cancel(2) and not sch.cancel(2)
+    assert [r.rid for r in sch.cancelled] == [2] and sch.cancelled[0].status == CANCELLED
+    sch.finish(a)
+    assert sch.next_batch() is None and not sch.waiting
+
+
+class SlowExecutor(FakeExecutor):
+    """One lane; each micro-batch takes 20 ms."""
+
+    def start(self, pairs, lane):
+        h = super().start(pairs, lane)
+        return (h[0] + 0.018, h[1])
+
+
+def test_serve_cancellations():
+    pairs = lambda i: np.array([[i, i + 1]], dtype=np.uint32)
+    # 0 runs first; 1 and 2 wait behind it; 3 arrives late
+    arrivals = [(0.0, pairs(0)), (0.001, pairs(1)), (0.001, pairs(2)), (0.08, pairs(3)), (0.08, pairs(4))]
+    # 0 is cancelled while on the device (its answer is dropped), 1 while
+    # waiting, 3 before it arrives; 9 does not exist; 4 after it finished
+    cancels = [(0.005, 0), (0.006, 1), (0.007, 3), (0.008, 9), (0.3, 4)]
+    ex = SlowExecutor()
+    sch = Scheduler(lanes=1, max_pairs=1, budget=10 ** 9, bytes_for=lambda p: p.shape[0])
+    out = serve(arrivals, ex, sch, cancels=cancels)
+    st = [r.status for r in out["requests"]]
+    assert st == [CANCELLED, CANCELLED, 0, CANCELLED, 0]
+    r = out["requests"]
+    assert r[0].result is None and r[1].result is None and r[1].start is None and r[3].start is None
+    assert r[2].result.tolist() == [5] and r[4].result.tolist() == [9]
+    assert out["cancelled"] == 3 and out["failed"] == 0 and out["queries"] == 2
+
+
+class FailingExecutor(FakeExecutor):
+    """The plan for a micro-batch holding vertex 666 cannot get device memory."""
+
+    class OOM(RuntimeError):
+        status = 3  # PPSP_ERR_OOM
+
+    def start(self, pairs, lane):
+        if (pairs == 666).any():
+            raise self.OOM("ppsp_plan_create: PPSP_ERR_OOM")
+        return super().start(pairs, lane)
+
+
+def test_serve_survives_a_failed_micro_batch():
+    arrivals = [(0.0, np.array([[1, 2]])), (0.001, np.array([[666, 3]])), (0.002, np.array([[4, 5]])),
+                (0.003, np.array([[1, 2]] * 9))]
+    # one pair per micro-batch: the failure stays with the request that caused it
+    sch = Scheduler(lanes=1, max_pairs=1, budget=10 ** 9, bytes_for=lambda p: p.shape[0])
+    out = serve(arrivals, FailingExecutor(), sch)
+    assert [r.status for r in out["requests"]] == [0, 3, 0, REJECTED]
+    assert out["failed"] == 1 and out["rejected"] == 1 and out["queries"] == 2
+    assert out["requests"][1].result is None and out["requests"][2].result.tolist() == [9]
+
+    class Broken(FakeExecutor):
+        def start(self, pairs, lane):
+            raise ValueError("not a library error")
+
+    with pytest.raises(ValueError):
+        serve(arrivals[:1], Broken(), Scheduler(lanes=1, max_pairs=4, budget=10, bytes_for=lambda p: 1))
 
 
 def test_memory_model_matches_slot_sizes():
