@@ -5,7 +5,9 @@ schedule): the batch strategy (Multi-BiDS, the per-component AUTO choice,
 Plain*, VC-SSSP: the per-batch choice of Sec. 4.3), threads per CTA, CTAs per
 pair team, CTAs per multi-search team,
 the sparse/dense frontier threshold (App. B), the distance layout of
-multi-search groups, and the frontier policy.  The tuner runs the batch's plan
+multi-search groups, the frontier policy, and the GetDist rule of the one-CTA
+path (Delta*-stepping, or rho-stepping / Bellman-Ford by merging buckets,
+Sec. 2).  The tuner runs the batch's plan
 with one knob changed at a time (coordinate descent from the library's
 defaults), keeps the fastest setting (minimum of a few device-timed runs),
 checks that every run returns the same distances, and caches the result per
@@ -26,14 +28,19 @@ from . import ppsp
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "tuning", "cache.json")
 
+# the library's defaults (ppsp_options_init), the starting point of the search
+DEFAULTS = {"strategy": "multi", "block_threads": 0, "team_ctas": 0, "big_team_ctas": 0, "dense_den": 0,
+            "layout": "auto", "frontier": "auto", "stepping_rho": 0}
+# knob -> the other values tried, in order
 SPACE = (
     ("strategy", ("auto", "plain_star", "vc")),
-    ("block_threads", (512, 256, 1024)),
-    ("team_ctas", (0, 1, 2, 4, 8)),
-    ("big_team_ctas", (0, 8, 16, 32, 64, 128)),
-    ("dense_den", (16, 4, 64, 1024)),
+    ("block_threads", (1024, 512, 256)),
+    ("team_ctas", (1, 2, 4, 8)),
+    ("big_team_ctas", (8, 16, 32, 64, 128)),
+    ("dense_den", (4, 64, 1024)),
     ("layout", ("interleaved", "stacked")),
-    ("frontier", ("auto", "sparse")),
+    ("frontier", ("sparse",)),
+    ("stepping_rho", (256, 1024)),
 )
 
 
@@ -84,7 +91,7 @@ def tune(G: ppsp.Graph, pairs: np.ndarray, mode: str, base: dict | None = None, 
         for v in values:
             if time.time() - t0 > budget_s:
                 break
-            if best.get(knob, None) == v or (knob not in best and v in (0, "auto", 512, "interleaved", 16)):
+            if best.get(knob, DEFAULTS[knob]) == v:
                 continue
             cand = dict(best)
             cand[knob] = v
