@@ -43,8 +43,15 @@ def _stale(out: str, deps: list) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
+    """Compile what is out of date and link lib/libppsp.so.  `extra` adds
+    nvcc flags (for example -DPPSP_PHASE_CLOCKS); objects built with other
+    flags are rebuilt, so a later plain build never keeps an instrumented one."""
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
+    stamp = os.path.join(BUILD, "flags.txt")
+    flags = " ".join([nvcc()] + ARCH + NVCC_FLAGS + (extra or []))
+    if not os.path.exists(stamp) or open(stamp).read() != flags:
+        force = True
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
     headers.append(os.path.join(INCLUDE, "ppsp.h"))
     srcs = sources()
@@ -72,6 +79,8 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
         tmp = LIB + f".tmp{os.getpid()}"
         run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"])
         os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(flags)
     return LIB
 
 
