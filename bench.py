@@ -133,6 +133,23 @@ def algorithmic_bytes(cnt: dict, dist_bytes: int, astar: bool) -> int:
                + P * 4 * 2 + T * dist_bytes)
 
 
+def group_time_stats(plan):
+    """Device time per group in the plan's last run (a pair group is one
+    query), summarised as the paper summarises query times (geometric mean),
+    with the median, 99th percentile and maximum, in ms."""
+    from paper_2506_16488_gb300 import ppsp
+
+    try:
+        ns = np.asarray(plan.group_times(), dtype=np.float64)
+    except ppsp.PPSPError:
+        return None
+    ms = ns[ns > 0] / 1e6
+    if ms.size == 0:
+        return None
+    return {"groups": int(ms.size), "geomean": float(np.exp(np.log(ms).mean())), "p50": float(np.median(ms)),
+            "p99": float(np.percentile(ms, 99)), "max": float(ms.max())}
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -311,6 +328,7 @@ def run_ours(args):
         counters.append(plan.sync())
     torch.cuda.synchronize()
     plan_used_graph = plan.uses_graph()
+    group_ms = group_time_stats(plan)  # the last timed step
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -357,9 +375,10 @@ def run_ours(args):
         pc = pp.sync()
         ms = e0.elapsed_time(e1)
         assert np.array_equal(po.cpu().numpy().view(np.uint64), got[psel])
+        qms = group_time_stats(pp)
         pp.close()
         return {"value": kp / (ms / 1000.0), "unit": "queries/s", "ms": ms, "queries": kp,
-                "gteps": pc["edges"] / (ms / 1000.0) / 1e9, "rounds": pc["rounds"]}
+                "gteps": pc["edges"] / (ms / 1000.0) / 1e9, "rounds": pc["rounds"], "query_ms": qms}
 
     # the plain baseline gets its best team size (fewer CTAs make the
     # per-step grid barrier cheaper; more give a step more parallelism)
@@ -442,6 +461,9 @@ def run_ours(args):
         "speedup_vs_plain_same_delta": qps / world / plain_same["value"],
         **({"strategies": compare} if compare else {}),
         "counters": cnt,
+        # per-group device time within the batch (start of its Init to the
+        # end of its tidy step on its team)
+        "group_ms": group_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": read_traffic(workload),

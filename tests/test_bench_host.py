@@ -100,3 +100,24 @@ def test_peaks_from_measured_file_or_fallback(tmp_path, monkeypatch):
     assert bench.read_peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6658.6}))
     assert bench.read_peaks() == (6658.6, "measured")
+
+
+def test_group_time_stats():
+    import numpy as np
+
+    from paper_2506_16488_gb300 import ppsp
+
+    class P:
+        def __init__(self, ns):
+            self.ns = ns
+
+        def group_times(self):
+            if self.ns is None:
+                raise ppsp.PPSPError(ppsp.ERR_INVALID_ARG)
+            return np.asarray(self.ns, dtype=np.uint64)
+
+    st = bench.group_time_stats(P([1_000_000, 4_000_000, 0, 16_000_000]))
+    assert st["groups"] == 3 and st["max"] == 16.0 and st["p50"] == 4.0
+    assert abs(st["geomean"] - 4.0) < 1e-12  # (1 * 4 * 16) ** (1/3)
+    assert bench.group_time_stats(P([0, 0])) is None
+    assert bench.group_time_stats(P(None)) is None
