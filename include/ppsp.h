@@ -225,8 +225,7 @@ ppsp_status ppsp_graph_get_info(const ppsp_graph* g, ppsp_graph_info* out);
  *             (0 if unreachable), also when the path did not fit (then the
  *             status is BUFFER_TOO_SMALL and dist_out is still valid)
  * Errors: INVALID_ARG (s or t >= n, bad options), NO_COORDS, UNSUPPORTED
- * (bidirectional mode on a directed graph; paths on a graph with zero-weight
- * edges), OOM, CUDA, TIMEOUT, OVERFLOW.
+ * (paths on a graph with zero-weight edges), OOM, CUDA, TIMEOUT, OVERFLOW.
  */
 ppsp_status ppsp_query(ppsp_graph* g, uint32_t s, uint32_t t, const ppsp_options* opt,
                        uint64_t* dist_out, uint32_t* path_buf, uint64_t path_cap,
@@ -243,7 +242,10 @@ ppsp_status ppsp_query(ppsp_graph* g, uint32_t s, uint32_t t, const ppsp_options
  *   path_lens     host uint64[k] or NULL: vertices on each path (needed length
  *                 if it did not fit; then the call returns BUFFER_TOO_SMALL)
  *   counters      host ppsp_counters or NULL: work done by the call
- * k = 0 is valid and does nothing.  Errors as ppsp_query.
+ * k = 0 is valid and does nothing.  Errors as ppsp_query, and UNSUPPORTED
+ * for paths with the SSSP strategies or for a multi-search group whose
+ * distance arrays would need 2^32 entries or more (use smaller groups:
+ * PPSP_BATCH_PLAIN_STAR or a smaller batch).
  */
 ppsp_status ppsp_batch(ppsp_graph* g, const uint32_t* pairs, uint64_t k, const ppsp_options* opt,
                        uint64_t* dists_out, uint32_t* paths_buf, const uint64_t* path_offsets,
