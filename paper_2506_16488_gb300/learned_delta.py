@@ -3,11 +3,15 @@
 The paper picks Delta for Delta*-stepping by doubling it until the geometric
 mean time stops improving (Sec. 6.1).  Here the same sweep produces training
 labels: every group of a batch is timed on the device (ppsp_plan_group_times)
-for Delta = Delta_default * 2^j over a grid of j, and its label is the j of
-its fastest run.  The model (12 -> 64 -> 64 -> 1, ppsp_delta_model_*) is
-trained with the library's own Adam kernel; its regret is the total group
-time at the predicted grid point over the total at each group's best grid
-point, minus one.  Delta never changes an answer (Theorems 3.3/3.4), so a bad
+for Delta = Delta_default * 2^j over a grid of j, and its label is the
+smallest j whose time is within 5% of its fastest run (time rises slowly
+below the best increment and steeply above it).  The model (12 -> 64 -> 64
+-> 1, ppsp_delta_model_*) is trained with the library's own Adam kernel, and
+a safety margin chosen on the training sets (the smallest that minimises
+their summed regret when a prediction between grid points is charged the
+larger increment) is subtracted from its output bias.  Its regret is the total
+group time at the predicted grid point over the total at each group's best
+grid point, minus one.  Delta never changes an answer (Theorems 3.3/3.4), so a bad
 prediction costs time only; without a model the library uses Delta_default
 (mean edge weight).
 
