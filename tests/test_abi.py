@@ -46,7 +46,6 @@ def test_options_defaults(lib):
     assert lib.ppsp_status_string(ppsp.ERR_TIMEOUT) == b"device wait timed out"
 
 
-
 def _create(lib, off, tgt, w, flags=1):
     h = ctypes.c_void_p()
     off = np.ascontiguousarray(off, dtype=np.uint64)
