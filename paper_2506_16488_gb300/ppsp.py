@@ -37,6 +37,8 @@ MLP_PARAMS = 5081
 
 
 class Options(ctypes.Structure):
+    """ppsp_options (include/ppsp.h), field for field; see make_options."""
+
     _fields_ = [
         ("mode", ctypes.c_int32),
         ("dist_bits", ctypes.c_int32),
@@ -60,6 +62,9 @@ class Options(ctypes.Structure):
 
 
 class Counters(ctypes.Structure):
+    """ppsp_counters: work done by one call (extracted X, edges E, relaxed R,
+    pushed P, rounds, groups, searches, touched, dense rounds)."""
+
     _fields_ = [(name, ctypes.c_uint64) for name in
                 ("extracted", "edges", "relaxed", "pushed", "rounds", "groups", "searches",
                  "touched", "dense_rounds")] + [("reserved", ctypes.c_uint64 * 7)]
@@ -69,6 +74,8 @@ class Counters(ctypes.Structure):
 
 
 class GraphInfo(ctypes.Structure):
+    """ppsp_graph_info: properties computed when the graph was created."""
+
     _fields_ = [
         ("n", ctypes.c_uint64), ("m", ctypes.c_uint64),
         ("w_min", ctypes.c_uint64), ("w_max", ctypes.c_uint64),
@@ -87,6 +94,8 @@ class GraphInfo(ctypes.Structure):
 
 
 class PPSPError(RuntimeError):
+    """A non-OK ppsp_status; ``status`` holds the code."""
+
     def __init__(self, status: int, what: str = ""):
         self.status = status
         name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
@@ -98,6 +107,7 @@ _lock = threading.Lock()
 
 
 def library_path() -> str:
+    """Path of the in-tree CUDA library (lib/libppsp.so)."""
     return _build.LIB
 
 
@@ -187,6 +197,10 @@ def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, 
                  big_team_ctas: int = 0, dense_den: int = 0, want_paths: bool = False, max_ctas: int = 0,
                  spin_limit: int = 0, stream: int | None = None, debug_flags: int = 0,
                  cuda_graph: bool = False, stepping_rho: int = 0) -> Options:
+    """ppsp_options from keyword arguments: the library's defaults
+    (ppsp_options_init) overridden by the given values; enum fields accept
+    names ("bidastar", "auto", ...) or numbers.  `stream` is a cudaStream_t
+    as an int (e.g. torch.cuda.Stream().cuda_stream)."""
     o = Options()
     load().ppsp_options_init(ctypes.byref(o))
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
@@ -231,6 +245,8 @@ class Graph:
 
     @classmethod
     def from_csr(cls, g, undirected: bool = True, with_coords: bool = True):
+        """From an object with offsets, targets, weights and coords (a
+        workloads.CSRGraph)."""
         return cls(g.offsets, g.targets, g.weights, g.coords if with_coords else None, undirected)
 
     def close(self):
@@ -261,11 +277,13 @@ class Graph:
         return self._h
 
     def info(self) -> dict:
+        """ppsp_graph_get_info as a dict."""
         gi = GraphInfo()
         _check(load().ppsp_graph_get_info(self._handle(), ctypes.byref(gi)), "ppsp_graph_get_info")
         return gi.as_dict()
 
     def query(self, s: int, t: int, **opts) -> int:
+        """d(s, t) (INF if unreachable) by ppsp_query; opts as make_options."""
         o = make_options(**opts)
         d = ctypes.c_uint64(0)
         plen = ctypes.c_uint64(0)
@@ -281,6 +299,8 @@ class Graph:
         return int(st), int(d.value)
 
     def batch(self, pairs, return_counters: bool = False, **opts):
+        """Distances of k pairs (uint64 [k], input order) by ppsp_batch, and
+        the work counters with return_counters=True."""
         o = make_options(**opts)
         pa = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
         k = pa.shape[0]
@@ -320,6 +340,7 @@ class Graph:
         return int(st), out, paths, lens
 
     def batch_status(self, pairs, **opts) -> tuple:
+        """(status, distances) without raising (for error-path tests)."""
         o = make_options(**opts)
         pa = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
         out = np.zeros(pa.shape[0], dtype=np.uint64)
@@ -328,6 +349,7 @@ class Graph:
         return int(st), out
 
     def plan(self, pairs, **opts) -> "Plan":
+        """A prepared batch (ppsp_plan_create) owned by this graph."""
         return Plan(self, pairs, **opts)
 
     def set_delta_model(self, mode: str | int, model: Optional["DeltaModel"]):
@@ -340,11 +362,13 @@ class Graph:
             model._graphs.add(self)
 
     def potential_coords(self) -> np.ndarray:
+        """Integer potential coordinates P(v) (int64 [n, 2])."""
         out = np.empty(2 * self.n, dtype=np.int64)
         _check(load().ppsp_potential_coords(self._handle(), _ptr(out)), "ppsp_potential_coords")
         return out.reshape(-1, 2)
 
     def potential_eval(self, anchor: int, vertices) -> np.ndarray:
+        """h_anchor(v) for the given vertices, computed on the device."""
         v = np.ascontiguousarray(vertices, dtype=np.uint32)
         out = np.empty(v.shape[0], dtype=np.int64)
         _check(load().ppsp_potential_eval(self._handle(), anchor, _ptr(v), v.shape[0], _ptr(out)),
@@ -372,9 +396,12 @@ class Plan:
         return self._h
 
     def run(self, d_out_ptr: int):
+        """Launch the batch on the plan's stream; distances go to the device
+        uint64 buffer at d_out_ptr (input order)."""
         _check(load().ppsp_plan_run(self._handle(), ctypes.c_void_p(d_out_ptr)), "ppsp_plan_run")
 
     def sync(self) -> dict:
+        """Wait for the last run; raise on a device error; its counters."""
         c = Counters()
         _check(load().ppsp_plan_sync(self._handle(), ctypes.byref(c)), "ppsp_plan_sync")
         return c.as_dict()
@@ -388,6 +415,7 @@ class Plan:
         return out
 
     def uses_graph(self) -> bool:
+        """Whether the last run replayed a captured CUDA graph."""
         v = ctypes.c_int32(0)
         _check(load().ppsp_plan_uses_graph(self._handle(), ctypes.byref(v)), "ppsp_plan_uses_graph")
         return bool(v.value)
@@ -437,11 +465,13 @@ class DeltaModel:
         return self._h
 
     def params(self) -> np.ndarray:
+        """The fp32 master copy of the parameters."""
         out = np.empty(MLP_PARAMS, dtype=np.float32)
         _check(load().ppsp_delta_model_get_params(self._handle(), _ptr(out)), "ppsp_delta_model_get_params")
         return out
 
     def predict(self, feats) -> np.ndarray:
+        """y = log2(Delta / Delta_default) per feature row."""
         f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MLP_FEATURES)
         out = np.empty(f.shape[0], dtype=np.float32)
         _check(load().ppsp_delta_model_predict(self._handle(), _ptr(f), f.shape[0], _ptr(out)),
@@ -449,6 +479,7 @@ class DeltaModel:
         return out
 
     def grad(self, feats, labels) -> tuple:
+        """(gradient of the mean squared error, the loss)."""
         f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MLP_FEATURES)
         y = np.ascontiguousarray(labels, dtype=np.float32)
         g = np.empty(MLP_PARAMS, dtype=np.float32)
@@ -458,6 +489,7 @@ class DeltaModel:
         return g, float(loss.value)
 
     def train(self, feats, labels, epochs: int, lr: float) -> float:
+        """Full-batch Adam steps on the device; the loss before the last."""
         f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MLP_FEATURES)
         y = np.ascontiguousarray(labels, dtype=np.float32)
         loss = ctypes.c_float(0)

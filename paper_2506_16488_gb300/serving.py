@@ -37,6 +37,9 @@ CANCELLED = -2
 
 @dataclass
 class Request:
+    """One client request: its pairs, arrival time and, once final, result
+    and status (0, REJECTED, CANCELLED or a library status)."""
+
     rid: int
     pairs: np.ndarray  # uint32 [k, 2]
     arrival: float
@@ -48,6 +51,8 @@ class Request:
 
 @dataclass
 class MicroBatch:
+    """Requests packed into one plan on one lane, with the bytes they hold."""
+
     requests: list
     pairs: np.ndarray
     bytes: int
@@ -78,6 +83,7 @@ class Scheduler:
         self.cancelled: list = []
 
     def add(self, req: Request):
+        """Queue a request, or reject it if it can never be admitted."""
         need = self.bytes_for(req.pairs)
         if need > self.budget or req.pairs.shape[0] > self.max_pairs:
             # can never be admitted in one piece: refuse instead of waiting forever
@@ -120,6 +126,7 @@ class Scheduler:
         return mb
 
     def finish(self, mb: MicroBatch):
+        """Return a finished micro-batch's lane and memory."""
         self.in_use -= mb.bytes
         self.free_lanes.append(mb.lane)
         self.free_lanes.sort()
@@ -261,6 +268,7 @@ class GpuExecutor:
         self.opts = opts
 
     def start(self, pairs: np.ndarray, lane: int):
+        """Create the micro-batch's plan and launch it on the lane's stream."""
         s = self.streams[lane]
         plan = self.graph.plan(pairs, mode=self.mode, dist_bits=self.dist_bits, stream=s.cuda_stream,
                                max_ctas=self.lane_ctas, **self.opts)
@@ -275,6 +283,7 @@ class GpuExecutor:
         return (plan, out, ev)
 
     def poll(self, handle):
+        """None while running, else (status, distances); frees the plan."""
         plan, out, ev = handle
         if not ev.query():
             return None

@@ -21,6 +21,10 @@ import numpy as np
 
 @dataclass
 class CSRGraph:
+    """A seeded synthetic graph in CSR form (an undirected edge is stored in
+    both directions), with the vertex coordinates and grid cells of the
+    grid-based recipes and the ids of the largest connected component."""
+
     n: int
     offsets: np.ndarray  # uint64 [n+1]
     targets: np.ndarray  # uint32 [m]

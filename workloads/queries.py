@@ -18,6 +18,7 @@ def _pool(g: CSRGraph) -> np.ndarray:
 
 
 def random_pairs(g: CSRGraph, k: int, seed: int) -> np.ndarray:
+    """k uniform random pairs of vertices of the largest component."""
     rng = np.random.default_rng(seed)
     pool = _pool(g)
     idx = rng.integers(0, pool.shape[0], size=(k, 2))
