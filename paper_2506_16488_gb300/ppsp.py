@@ -298,13 +298,18 @@ class Graph:
         st = load().ppsp_query(self._handle(), s, t, ctypes.byref(o), ctypes.byref(d), None, 0, None)
         return int(st), int(d.value)
 
-    def batch(self, pairs, return_counters: bool = False, **opts):
+    def batch(self, pairs, return_counters: bool = False, out: Optional[np.ndarray] = None, **opts):
         """Distances of k pairs (uint64 [k], input order) by ppsp_batch, and
-        the work counters with return_counters=True."""
+        the work counters with return_counters=True.  `out` (optional) is a
+        caller-owned contiguous uint64 [k] array to write them to, e.g. in
+        pinned host memory; contiguous uint32 pairs are read in place."""
         o = make_options(**opts)
         pa = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
         k = pa.shape[0]
-        out = np.zeros(k, dtype=np.uint64)
+        if out is None:
+            out = np.zeros(k, dtype=np.uint64)
+        elif out.dtype != np.uint64 or out.shape != (k,) or not out.flags.c_contiguous:
+            raise ValueError(f"out must be a contiguous uint64 array of {k} elements")
         c = Counters()
         st = load().ppsp_batch(self._handle(), _ptr(pa), k, ctypes.byref(o), _ptr(out), None, None, None,
                                ctypes.byref(c))

@@ -44,6 +44,14 @@ class FakeLib:
         assert ("graph", g.value) in self.live
         return self._new("plan", out)
 
+    def ppsp_batch(self, g, pairs, k, opt, out, paths, offs, lens, cnt):
+        assert ("graph", g.value) in self.live
+        self.calls.append(("batch", pairs.value, out.value))
+        arr = ctypes.cast(out, ctypes.POINTER(ctypes.c_uint64))
+        for q in range(k):
+            arr[q] = 7 + q
+        return ppsp.OK
+
     def ppsp_plan_destroy(self, h):
         self._free("plan", h)
 
@@ -120,3 +128,18 @@ def test_model_outlives_graph(fake):
     assert not fake.live
     with pytest.raises(ValueError):
         ppsp.DeltaModel(np.ones(7, np.float32))
+
+
+def test_batch_writes_a_caller_buffer(fake):
+    g = _graph()
+    pairs = np.array([[0, 1], [1, 0], [1, 1]], dtype=np.uint32)
+    out = np.zeros(3, dtype=np.uint64)
+    res = g.batch(pairs, out=out)
+    assert res is out and out.tolist() == [7, 8, 9]
+    call = [c for c in fake.calls if c[0] == "batch"][-1]
+    assert call[1] == pairs.ctypes.data and call[2] == out.ctypes.data  # read and written in place
+    assert g.batch(pairs).tolist() == [7, 8, 9]
+    for bad in (np.zeros(3, np.int64), np.zeros(4, np.uint64), np.zeros(6, np.uint64)[::2]):
+        with pytest.raises(ValueError):
+            g.batch(pairs, out=bad)
+    g.close()
