@@ -10,7 +10,7 @@ Reported:
   value        queries/sec with the graph, the pairs and the output in HBM
                (CUDA events on the launching stream around each step; the L2
                is flushed between steps by writing a 256 MB buffer)
-  e2e          queries/sec through ppsp_batch with host buffers (query graph
+  e2e          queries/sec through ppsp_batch with pinned host buffers (query graph
                build, host->device copy of the pairs, search, device->host
                copy of the distances inside the timed region)
   plain        the same queries one at a time on the whole GPU (Plain-BiDS)
