@@ -340,9 +340,8 @@ def run_ours(args):
         total_ms = float(t.item())
     got = out.cpu().numpy().view(np.uint64)
 
-    # e2e through the C ABI with host buffers
-    # the host buffers live in pinned (page-locked) memory, as a serving
-    # process keeps them; pageable memory if pinning is refused
+    # e2e through the C ABI with host buffers, in pinned (page-locked)
+    # memory as a serving process keeps them (pageable if pinning is refused)
     try:
         t_pairs = torch.from_numpy(np.ascontiguousarray(pairs, dtype=np.uint32).view(np.int32)).pin_memory()
         t_res = torch.empty(k, dtype=torch.int64).pin_memory()
