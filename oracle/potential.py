@@ -76,3 +76,77 @@ def consistent_for_anchor(off: np.ndarray, tgt: np.ndarray, w: np.ndarray, h: np
     n = off.shape[0] - 1
     src = np.repeat(np.arange(n, dtype=np.int64), np.diff(off).astype(np.int64))
     return bool(np.all(h[src] <= w.astype(np.int64) + h[tgt.astype(np.int64)]))
+
+
+MAX_SHIFT = 8          # at most 8 fixed-point bits
+COORD_LIMIT = 2 ** 30  # |P(v)| stays below 2^30, so squared differences fit 63 bits
+SHRINK_ATTEMPTS = 40   # the margin doubles at most this many times
+
+
+def _edge_sources(off: np.ndarray) -> np.ndarray:
+    n = off.shape[0] - 1
+    return np.repeat(np.arange(n, dtype=np.int64), np.diff(off).astype(np.int64))
+
+
+def certificate_ok_exact(off: np.ndarray, tgt: np.ndarray, w: np.ndarray, P: np.ndarray,
+                         shift: int) -> bool:
+    """The certificate dX^2 + dY^2 <= (2^F w)^2 on every edge, in exact
+    unsigned 64-bit arithmetic (|P| < 2^30 keeps the left side below 2^63;
+    a right side of 2^64 or more holds for any left side)."""
+    src = _edge_sources(off)
+    d = P[src] - P[tgt.astype(np.int64)]
+    lhs = (d[:, 0] * d[:, 0]).astype(np.uint64) + (d[:, 1] * d[:, 1]).astype(np.uint64)
+    sw = w.astype(np.uint64) << np.uint64(shift)
+    big = sw >= np.uint64(1 << 32)
+    rhs = np.where(big, np.uint64(0), sw * sw)
+    return bool(np.all(big | (lhs <= rhs)))
+
+
+def choose_scale(off: np.ndarray, tgt: np.ndarray, w: np.ndarray, coords: np.ndarray):
+    """Scale c, shift F and coordinates P of the certified potential, by the
+    rule the library states for graph creation (Sec. 3.3, Fact 3.1), written
+    out step by step in float64:
+
+    1. over the edges of positive Euclidean length l (float64 of the float32
+       coordinates): c_max = min w / l and w_min = min w; a zero weight on
+       such an edge admits no positive scale (c = 0: the potential is 0);
+    2. F = the largest shift <= 8 with a_max * c_max * 2^F < 2^30, a_max the
+       largest absolute coordinate (none: c = 0);
+    3. margin e = 2 / (2^F w_min); try c = c_max (1 - e), P = floor(p 2^F c
+       + 0.5), and double e until the certificate holds on every edge (at
+       most 40 times; else c = 0).
+
+    Returns (c, F, P int64 [n, 2]); c = 0 comes with F = 0 and P = 0.
+    """
+    off = np.asarray(off, dtype=np.uint64)
+    tgt = np.asarray(tgt, dtype=np.uint32)
+    w = np.asarray(w, dtype=np.uint32)
+    p = np.asarray(coords, dtype=np.float32).astype(np.float64)
+    n = p.shape[0]
+    none = (0.0, 0, np.zeros((n, 2), dtype=np.int64))
+    src = _edge_sources(off)
+    d = p[src] - p[tgt.astype(np.int64)]
+    ell = np.sqrt(d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1])
+    pos = ell > 0.0
+    if not np.any(pos) or np.any(w[pos] == 0):
+        return none
+    c_max = float(np.min(w[pos].astype(np.float64) / ell[pos]))
+    w_min = int(np.min(w[pos]))
+    a_max = float(np.max(np.abs(p))) if n else 0.0
+    if a_max == 0.0 or not np.isfinite(c_max) or c_max <= 0.0:
+        return none
+    F = MAX_SHIFT
+    while F > 0 and a_max * c_max * float(2 ** F) >= float(COORD_LIMIT):
+        F -= 1
+    if a_max * c_max * float(2 ** F) >= float(COORD_LIMIT):
+        return none
+    e = 2.0 / (float(2 ** F) * float(max(1, w_min)))
+    for _ in range(SHRINK_ATTEMPTS):
+        c = c_max * (1.0 - e)
+        if c <= 0.0:
+            break
+        P = np.floor(p * (float(2 ** F) * c) + 0.5).astype(np.int64)
+        if certificate_ok_exact(off, tgt, w, P, F):
+            return c, F, P
+        e *= 2.0
+    return none

@@ -125,6 +125,10 @@ def test_potential_is_consistent_on_directed_edges(one_way):
     g, pairs, want, G = one_way
     P = G.potential_coords()
     info = G.info()
+    # the same creation rule, applied by the oracle to the directed CSR
+    c, F, P_ref = opot.choose_scale(g.offsets, g.targets, g.weights, g.coords)
+    assert (info["potential_scale"], info["potential_shift"]) == (c, F)
+    assert np.array_equal(P, P_ref)
     rng = np.random.default_rng(5)
     for anchor in rng.choice(g.n, size=4, replace=False):
         h = opot.h_all(P, int(anchor), int(info["potential_shift"]))

@@ -210,12 +210,14 @@ def test_timeout_hook_returns_status_and_recovers(cfg1):
 
 def test_potential_matches_oracle():
     g = road_like_graph(96, seed=51)
+    # the oracle chooses c, F and P by the creation rule on its own; nothing
+    # is taken from the library
+    c, F, P = opot.choose_scale(g.offsets, g.targets, g.weights, g.coords)
+    assert 0.99 * 1000 < c <= 1000.0 and F >= 1
     with ppsp.Graph.from_csr(g) as G:
         info = G.info()
-        c, F = info["potential_scale"], info["potential_shift"]
-        assert 0.99 * 1000 < c <= 1000.0 and F >= 1
-        P = G.potential_coords()
-        assert np.array_equal(P, opot.potential_coords(g.coords, c, F))
+        assert info["potential_scale"] == c and info["potential_shift"] == F
+        assert np.array_equal(G.potential_coords(), P)
         assert opot.certificate_ok(g.offsets, g.targets, g.weights, P, F).all()
         rng = np.random.default_rng(2)
         verts = rng.integers(0, g.n, size=2000).astype(np.uint32)

@@ -97,3 +97,46 @@ def test_adam_reduces_loss_on_a_linear_target():
     assert last < 0.05 * first
     # mean and std are never moved (their gradient is zero)
     assert np.array_equal(p[:24], _params(np.random.default_rng(2), scale=0.2)[:24])
+
+
+def test_adam_two_steps_worked_by_hand():
+    """Two Adam steps (Kingma & Ba, 2015) on a 3-parameter vector from p = 0,
+    beta1 = 0.9, beta2 = 0.999, lr = 0.1, eps = 1e-8, worked out by hand:
+
+    step 1, g1 = (1, -2, 1/2):
+      m1 = 0.1 g1 = (1/10, -1/5, 1/20);  v1 = 0.001 g1^2 = (1/1000, 1/250, 1/4000)
+      m_hat = m1 / 0.1 = g1;  v_hat = v1 / 0.001 = g1^2 = (1, 4, 1/4)
+      p1 = -lr g1 / (|g1| + eps) = (-0.1/(1+eps), 0.2/(2+eps), -0.05/(1/2+eps))
+    step 2, g2 = (3, 0, -1):
+      m2 = 0.9 m1 + 0.1 g2 = (39/100, -9/50, -11/200)
+      v2 = 0.999 v1 + 0.001 g2^2 = (9999/10^6, 999/250000, 4999/(4 10^6))
+      1 - 0.9^2 = 19/100;  1 - 0.999^2 = 1999/10^6
+      m_hat = (39/19, -18/19, -11/38);  v_hat = (9999/1999, 3996/1999, 4999/7996)
+      p2 = p1 - lr m_hat / (sqrt(v_hat) + eps)
+
+    Swapped betas leave step 1 unchanged but not step 2; a missing bias
+    correction or sqrt(v) without the correction changes step 1.
+    """
+    eps = 1e-8
+    p1_want = np.array([-0.1 / (1 + eps), 0.2 / (2 + eps), -0.05 / (0.5 + eps)])
+    mh2 = np.array([39 / 19, -18 / 19, -11 / 38])
+    vh2 = np.array([9999 / 1999, 3996 / 1999, 4999 / 7996])
+    p2_want = p1_want - 0.1 * mh2 / (np.sqrt(vh2) + eps)
+    m2_want = np.array([39 / 100, -9 / 50, -11 / 200])
+    v2_want = np.array([9999e-6, 999 / 250000, 4999 / 4e6])
+
+    p, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    p, m, v = mlp.adam_step(p, m, v, np.array([1.0, -2.0, 0.5]), 1, 0.1)
+    assert np.allclose(m, [0.1, -0.2, 0.05], rtol=1e-14, atol=0)
+    assert np.allclose(v, [1e-3, 4e-3, 2.5e-4], rtol=1e-12, atol=0)
+    assert np.allclose(p, p1_want, rtol=1e-12, atol=0)
+    p, m, v = mlp.adam_step(p, m, v, np.array([3.0, 0.0, -1.0]), 2, 0.1)
+    assert np.allclose(m, m2_want, rtol=1e-12, atol=0)
+    assert np.allclose(v, v2_want, rtol=1e-12, atol=0)
+    assert np.allclose(p, p2_want, rtol=1e-12, atol=0)
+    # swapped betas: the same first step, a different second one
+    q, mq, vq = mlp.adam_step(np.zeros(3), np.zeros(3), np.zeros(3), np.array([1.0, -2.0, 0.5]), 1, 0.1,
+                              b1=0.999, b2=0.9)
+    assert np.allclose(q, p1_want, rtol=1e-9, atol=0)
+    q, mq, vq = mlp.adam_step(q, mq, vq, np.array([3.0, 0.0, -1.0]), 2, 0.1, b1=0.999, b2=0.9)
+    assert np.max(np.abs(q - p2_want)) > 1e-3
