@@ -523,13 +523,13 @@ def run_serving(args):
     src = lambda k: g.lcc[rng.integers(0, g.lcc.shape[0], size=(k, 2))]
     ex = GpuExecutor(G, lanes, mode=mode, dist_bits=64, lane_ctas=lane_ctas, team_ctas=args.team_ctas)
     # warm-up: slot pool and code paths
-    serve(poisson_arrivals(2000, 0.2, src, seed=5004), ex, Scheduler(lanes, 256, budget, memory_model(g.n, lane_ctas, 64)))
+    serve(poisson_arrivals(2000, 0.2, src, seed=5004), ex, Scheduler(lanes, 256, budget, memory_model(ex.slot_bytes(), lane_ctas)))
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
     sampler.start()
     rates = []
     for rate in args.rates:
         arr = poisson_arrivals(rate, args.duration, src, seed=int(rate))
-        out = serve(arr, ex, Scheduler(lanes, 256, budget, memory_model(g.n, lane_ctas, 64)))
+        out = serve(arr, ex, Scheduler(lanes, 256, budget, memory_model(ex.slot_bytes(), lane_ctas)))
         bad = [r for r in out["requests"] if r.status != 0]
         rates.append({"offered_qps": rate, "sustained_qps": out["qps"], "p50_ms": out["latency_p50_ms"],
                       "p99_ms": out["latency_p99_ms"], "queries": out["queries"], "requests": len(arr),

@@ -311,6 +311,32 @@ ppsp_status ppsp_plan_features(const ppsp_plan* p, float* out, uint64_t cap, uin
  */
 ppsp_status ppsp_plan_group_times(ppsp_plan* p, uint64_t* out_ns, uint64_t cap, uint64_t* ngroups);
 
+/*
+ * Device memory of a plan (host outputs, each nullable):
+ *   slot_bytes   search memory of its teams (one slot per team: distances,
+ *                frontier bitmaps and queues, touched list, bucket overflow);
+ *                slots come from the graph's pool and go back to it when the
+ *                plan is destroyed
+ *   teams        number of teams, that is of slots held
+ *   other_bytes  descriptors, per-query state and path buffers of the plan
+ * Errors: INVALID_ARG.
+ */
+ppsp_status ppsp_plan_device_bytes(const ppsp_plan* p, uint64_t* slot_bytes, uint64_t* teams,
+                                   uint64_t* other_bytes);
+
+/*
+ * Device bytes of the slot one team of a batch allocates for groups of
+ * `searches` searches (2 for a BiDS pair, 1 for an SSSP-based or
+ * one-directional search, up to 64 for a Multi-BiDS group) with the given
+ * distance width (32 or 64) and frontier policy, on a team smaller than the
+ * whole GPU.  A batch plan holds one slot per team, and at most as many
+ * teams as groups, so admission control can bound a batch's search memory
+ * before creating its plan (host only, no device work).
+ * Errors: INVALID_ARG.
+ */
+ppsp_status ppsp_slot_bytes(const ppsp_graph* g, uint32_t searches, int32_t dist_bits, int32_t frontier,
+                            uint64_t* out);
+
 /* 1 if the plan's last run replayed a captured CUDA graph, else 0. */
 ppsp_status ppsp_plan_uses_graph(const ppsp_plan* p, int32_t* out);
 
@@ -393,7 +419,9 @@ ppsp_status ppsp_graph_set_delta_model(ppsp_graph* g, int32_t mode, ppsp_delta_m
  * the one array: calls that overlap on the GPU race and must not be issued.
  * The first call on a device resolves the array's address and initialises it;
  * make that call before any stream capture.  Errors: INVALID_ARG (null
- * pointers, n above the limit, ids >= n), CUDA, TIMEOUT, OVERFLOW.
+ * pointers, n above the limit, ids >= n, d_offsets not 4-byte aligned,
+ * d_edges or d_dist_out not 8-byte aligned), UNSUPPORTED (a device on which
+ * fewer than two engine CTAs fit), CUDA, TIMEOUT, OVERFLOW.
  */
 #define PPSP_NOALLOC_MAX_N (1u << 20)
 ppsp_status ppsp_query_noalloc(const uint32_t* d_offsets, const uint32_t* d_edges, uint32_t n, uint64_t m,

@@ -36,6 +36,8 @@
 // update reads both final values.
 #include <cooperative_groups.h>
 
+#include <atomic>
+
 #include "ppsp_internal.h"
 
 namespace cg = cooperative_groups;
@@ -1758,14 +1760,18 @@ __global__ void __launch_bounds__(B, (PPSP_ENGINE_SM_THREADS / B) > 0 ? (PPSP_EN
 // ----------------------------------------------------------------------------
 // host side
 // ----------------------------------------------------------------------------
+// The dynamic shared-memory limit is an attribute of the function on the
+// current device: it is set once per instantiation and device.
+constexpr int SMEM_ATTR_DEVICES = 64;
 template <typename D, int B, bool LOCAL>
 static ppsp_status set_smem_attr() {
-    static bool done = false;  // per instantiation; the attribute is per device function
-    if (!done) {
-        PPSP_CUDA_TRY(cudaFuncSetAttribute(engine_kernel<D, B, LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)engine_smem_bytes<D, B>()));
-        done = true;
-    }
+    static std::atomic<bool> done[SMEM_ATTR_DEVICES];
+    int dev = 0;
+    PPSP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < SMEM_ATTR_DEVICES && done[dev].load(std::memory_order_acquire)) return PPSP_OK;
+    PPSP_CUDA_TRY(cudaFuncSetAttribute(engine_kernel<D, B, LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)engine_smem_bytes<D, B>()));
+    if (dev >= 0 && dev < SMEM_ATTR_DEVICES) done[dev].store(true, std::memory_order_release);
     return PPSP_OK;
 }
 

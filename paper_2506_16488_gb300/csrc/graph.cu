@@ -148,6 +148,43 @@ static bool check_symmetric(u64 n, const u64* off, const u32* tgt, const u32* w)
     return ok;
 }
 
+SlotCaps slot_caps(u64 range, int frontier, bool whole_gpu) {
+    u64 fc = std::max<u64>(range, 64);
+    fc = (fc + 63) & ~63ull;
+    SlotCaps c;
+    c.flat_cap = fc;
+    c.qcap = (frontier == PPSP_FRONTIER_SPARSE) ? (u32)fc : (u32)std::min<u64>(fc, fc / 8 + 4096);
+    c.tcap = whole_gpu ? (u32)fc : (u32)std::min<u64>(fc, fc / 4 + 4096);
+    return c;
+}
+
+namespace {
+struct SlotLayout {
+    u64 ocap, b_dist, b_bm, b_q, b_fd, b_t, b_st, b_of, b_od, total;
+};
+SlotLayout slot_layout(int dist_bits, u64 flat_cap, u32 qcap, u32 tcap) {
+    const u64 W = dist_bits / 8;
+    const u64 words = (flat_cap + 31) / 32;
+    auto al = [](u64 x) { return (x + 255) & ~255ull; };
+    SlotLayout L;
+    L.ocap = std::max<u64>(32 * 256, flat_cap / 4) / 32 * 32;
+    L.b_dist = al(flat_cap * W);
+    L.b_bm = al(words * 4);
+    L.b_q = al((u64)qcap * 4);
+    L.b_fd = al((u64)qcap * W);
+    L.b_t = al((u64)tcap * 4);
+    L.b_st = al(sizeof(SlotState));
+    L.b_of = al(L.ocap * 4);
+    L.b_od = al(L.ocap * W);
+    L.total = L.b_dist + 2 * L.b_bm + 2 * L.b_q + 2 * L.b_fd + L.b_t + L.b_st + L.b_of + L.b_od;
+    return L;
+}
+}  // namespace
+
+u64 slot_alloc_bytes(int dist_bits, u64 flat_cap, u32 qcap, u32 tcap) {
+    return slot_layout(dist_bits, flat_cap, qcap, tcap).total;
+}
+
 ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, Slot** out) {
     SlotKey key{dist_bits, flat_cap, qcap, tcap};
     for (auto it = g->pool.lower_bound(key); it != g->pool.end(); ++it) {
@@ -160,14 +197,10 @@ ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u
         }
     }
     auto s = std::make_unique<Slot>();
-    const u64 W = dist_bits / 8;
-    const u64 words = (flat_cap + 31) / 32;
-    auto al = [](u64 x) { return (x + 255) & ~255ull; };
-    const u64 ocap = std::max<u64>(32 * 256, flat_cap / 4) / 32 * 32;
-    const u64 b_dist = al(flat_cap * W), b_bm = al(words * 4), b_q = al((u64)qcap * 4),
-              b_fd = al((u64)qcap * W), b_t = al((u64)tcap * 4), b_st = al(sizeof(SlotState)),
-              b_of = al(ocap * 4), b_od = al(ocap * W);
-    s->bytes = b_dist + 2 * b_bm + 2 * b_q + 2 * b_fd + b_t + b_st + b_of + b_od;
+    const SlotLayout L = slot_layout(dist_bits, flat_cap, qcap, tcap);
+    const u64 ocap = L.ocap, b_dist = L.b_dist, b_bm = L.b_bm, b_q = L.b_q, b_fd = L.b_fd, b_t = L.b_t,
+              b_st = L.b_st, b_of = L.b_of, b_od = L.b_od;
+    s->bytes = L.total;
     cudaError_t e = cudaMalloc(&s->base, s->bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();

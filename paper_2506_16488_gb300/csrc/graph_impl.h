@@ -73,6 +73,17 @@ struct ppsp_graph {
 
 namespace ppsp {
 
+// Capacities of the slot of a team whose groups span `range` flat entries
+// (searches x n): frontier queues, touched list (a whole-GPU team never
+// overflows its touched list).
+struct SlotCaps {
+    u64 flat_cap;
+    u32 qcap, tcap;
+};
+SlotCaps slot_caps(u64 range, int frontier, bool whole_gpu);
+// Device bytes of a freshly allocated slot with these capacities.
+u64 slot_alloc_bytes(int dist_bits, u64 flat_cap, u32 qcap, u32 tcap);
+
 // Borrow a slot with at least the requested capacities (allocating if needed).
 ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, Slot** out);
 void slot_release(ppsp_graph* g, Slot* s);

@@ -155,6 +155,11 @@ extern "C" ppsp_status ppsp_query_noalloc(const uint32_t* d_offsets, const uint3
                                           uint64_t* d_dist_out, void* stream) {
     if (!d_offsets || (m && !d_edges) || !d_dist_out) return PPSP_ERR_INVALID_ARG;
     if (n == 0 || n > NA_MAX_N || m >= 0xFFFFFFFFull || s >= n || t >= n) return PPSP_ERR_INVALID_ARG;
+    // the kernels read offsets as 4-byte words, adjacency records as 8-byte
+    // pairs and write the answer as one 8-byte word: a misaligned pointer
+    // would fault on the device, so it is refused here
+    if (((uintptr_t)d_offsets & 3u) || ((uintptr_t)d_edges & 7u) || ((uintptr_t)d_dist_out & 7u))
+        return PPSP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_na_mu);
     int dev = 0;
@@ -179,7 +184,9 @@ extern "C" ppsp_status ppsp_query_noalloc(const uint32_t* d_offsets, const uint3
     ppsp_status rs = engine_occupancy(32, 512, &bpsm, &sms);
     if (rs != PPSP_OK) return rs;
     u32 grid = (u32)std::min<long long>((long long)bpsm * sms, NA_MAX_CTAS);
-    if (grid == 0) return PPSP_ERR_UNSUPPORTED;
+    // the one team must span at least two CTAs: a one-CTA team would take the
+    // bucketed path, whose overflow and far lists this scratch does not hold
+    if (grid < 2) return PPSP_ERR_UNSUPPORTED;
 
     PPSP_CUDA_TRY(cudaMemsetAsync(base + O_RUN, 0, RUN_BYTES, st));
     if (delta == 0 && m) {
@@ -227,7 +234,10 @@ extern "C" ppsp_status ppsp_query_noalloc(const uint32_t* d_offsets, const uint3
         return rs;
     }
     rs = launch_scatter(reinterpret_cast<const u32*>(base + O_MAP), a.mu, 1, d_dist_out, st);
-    if (rs != PPSP_OK) return rs;
+    if (rs != PPSP_OK) {
+        g_na_dirty[dev] = true;  // the engine may have run: scrub before the next call
+        return rs;
+    }
     u32 err = 0;
     PPSP_CUDA_TRY(cudaMemcpyAsync(&err, base + O_ERR, 4, cudaMemcpyDeviceToHost, st));
     PPSP_CUDA_TRY(cudaStreamSynchronize(st));

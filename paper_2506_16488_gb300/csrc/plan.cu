@@ -722,7 +722,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         if (g_big) {
             nbt = std::min<u32>((u32)big.size(), g_big);
             tb = o.big_team_ctas ? std::min<u32>((u32)o.big_team_ctas, g_big) : g_big / nbt;
-            nbt = std::max<u32>(1, g_big / tb);
+            nbt = std::max<u32>(1, std::min<u32>(g_big / tb, (u32)big.size()));
             for (u32 t = 0; t < nbt; ++t) teams.push_back({tb, 0});
         }
         u32 g_small = grid - nbt * tb;
@@ -731,7 +731,8 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
             u32 ts_auto = 1;
             while (ts_auto * 2 <= 32 && (u64)ts_auto * 2 * small.size() <= g_small) ts_auto *= 2;
             u32 ts = o.team_ctas ? std::min<u32>((u32)o.team_ctas, g_small) : ts_auto;
-            u32 nst = std::max<u32>(1, g_small / ts);
+            // no more teams than groups: an idle team would still hold a slot
+            u32 nst = std::max<u32>(1, std::min<u32>(g_small / ts, (u32)small.size()));
             for (u32 t = 0; t < nst; ++t) teams.push_back({ts, 1});
             g_small = nst * ts;
         } else {
@@ -783,13 +784,9 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
             range_q[qd] = std::max(range_q[qd], range);
         }
     for (u32 t = 0; t < teams.size(); ++t) {
-        u64 fc = std::max<u64>(range_q[teams[t].queue], 64);
-        fc = (fc + 63) & ~63ull;
-        u32 qcap = (o.frontier == PPSP_FRONTIER_SPARSE) ? (u32)fc : (u32)std::min<u64>(fc, fc / 8 + 4096);
-        u32 tcap = (u32)std::min<u64>(fc, fc / 4 + 4096);
-        if (teams[t].size == grid) tcap = (u32)fc;  // whole-GPU team: never overflow
+        const SlotCaps sc = slot_caps(range_q[teams[t].queue], o.frontier, teams[t].size == grid);
         Slot* s = nullptr;
-        st = slot_acquire(g, o.dist_bits, fc, qcap, tcap, &s);
+        st = slot_acquire(g, o.dist_bits, sc.flat_cap, sc.qcap, sc.tcap, &s);
         if (st != PPSP_OK) {
             for (Slot* x : P->slots) slot_release(g, x);
             return st;
@@ -1120,6 +1117,36 @@ ppsp_status ppsp_batch_sources(const uint32_t* pairs, uint64_t k, int32_t strate
         if (dir_out) dir_out[q] = (map[q] == NONE) ? 0u : src[map[q]].dir;
     }
     *n_sources = distinct.size();
+    return PPSP_OK;
+}
+
+ppsp_status ppsp_plan_device_bytes(const ppsp_plan* p, uint64_t* slot_bytes, uint64_t* teams,
+                                   uint64_t* other_bytes) {
+    if (!p) return PPSP_ERR_INVALID_ARG;
+    u64 sb = 0;
+    for (const Slot* s : p->slots) sb += s->bytes;
+    u64 ob = p->arena_bytes;
+    if (p->d_paths) {
+        const u64 NQ = p->qedges.size();
+        auto al = [](u64 x) { return (x + 255) & ~255ull; };
+        ob += std::max<u64>(256, al(p->path_off[NQ] * 4) + al((NQ + 1) * 8) + al(NQ * 8) + al(NQ * 4));
+    }
+    if (slot_bytes) *slot_bytes = sb;
+    if (teams) *teams = p->slots.size();
+    if (other_bytes) *other_bytes = ob;
+    return PPSP_OK;
+}
+
+ppsp_status ppsp_slot_bytes(const ppsp_graph* g, uint32_t searches, int32_t dist_bits, int32_t frontier,
+                            uint64_t* out) {
+    if (!g || !out || searches == 0 || searches > (u32)KMAX) return PPSP_ERR_INVALID_ARG;
+    if (dist_bits != 32 && dist_bits != 64) return PPSP_ERR_INVALID_ARG;
+    if (frontier < PPSP_FRONTIER_AUTO || frontier > PPSP_FRONTIER_DENSE) return PPSP_ERR_INVALID_ARG;
+    // the plan's layouts: a group of k searches spans n * 2^ceil(log2 k)
+    // interleaved entries (k entries per vertex for pairs and singles)
+    const u64 range = (u64)g->n << ceil_log2(searches);
+    const SlotCaps sc = slot_caps(range, frontier, false);
+    *out = slot_alloc_bytes(dist_bits, sc.flat_cap, sc.qcap, sc.tcap);
     return PPSP_OK;
 }
 

@@ -142,6 +142,8 @@ def load(build_if_missing: bool = False):
             "ppsp_plan_features": (S, [p, p, u64, p]),
             "ppsp_plan_group_times": (S, [p, p, u64, p]),
             "ppsp_plan_uses_graph": (S, [p, p]),
+            "ppsp_plan_device_bytes": (S, [p, p, p, p]),
+            "ppsp_slot_bytes": (S, [p, u32, i32, i32, p]),
             "ppsp_batch_sources": (S, [p, u64, i32, u32, p, p, p]),
             "ppsp_delta_model_create": (S, [p, p]),
             "ppsp_delta_model_destroy": (None, [p]),
@@ -357,6 +359,14 @@ class Graph:
         """A prepared batch (ppsp_plan_create) owned by this graph."""
         return Plan(self, pairs, **opts)
 
+    def slot_bytes(self, searches: int = 2, dist_bits: int = 32, frontier="auto") -> int:
+        """Device bytes of the slot one team of a batch allocates for groups
+        of `searches` searches (ppsp_slot_bytes; host only)."""
+        out = ctypes.c_uint64(0)
+        f = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
+        _check(load().ppsp_slot_bytes(self._handle(), searches, dist_bits, f, ctypes.byref(out)), "ppsp_slot_bytes")
+        return int(out.value)
+
     def set_delta_model(self, mode: str | int, model: Optional["DeltaModel"]):
         """Plans of this mode with delta=0 use the model (kept alive by the graph)."""
         m = MODES[mode] if isinstance(mode, str) else int(mode)
@@ -418,6 +428,14 @@ class Plan:
         out = np.zeros((ng.value, MLP_FEATURES), dtype=np.float32)
         _check(load().ppsp_plan_features(self._handle(), _ptr(out), ng.value, ctypes.byref(ng)), "ppsp_plan_features")
         return out
+
+    def device_bytes(self) -> dict:
+        """Device memory the plan holds (ppsp_plan_device_bytes): its teams'
+        slots (one per team) and the rest (descriptors, paths)."""
+        sb, nt, ob = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(load().ppsp_plan_device_bytes(self._handle(), ctypes.byref(sb), ctypes.byref(nt), ctypes.byref(ob)),
+               "ppsp_plan_device_bytes")
+        return {"slot_bytes": int(sb.value), "teams": int(nt.value), "other_bytes": int(ob.value)}
 
     def uses_graph(self) -> bool:
         """Whether the last run replayed a captured CUDA graph."""

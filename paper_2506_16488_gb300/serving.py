@@ -253,7 +253,8 @@ def poisson_arrivals(rate_qps: float, duration_s: float, pair_source: Callable[[
 class GpuExecutor:
     """Runs a micro-batch as one plan on a lane's stream with lane_ctas CTAs."""
 
-    def __init__(self, graph, lanes: int, mode: str = "bids", dist_bits: int = 32, lane_ctas: int = 0, **opts):
+    def __init__(self, graph, lanes: int, mode: str = "bids", dist_bits: int = 32, lane_ctas: int = 0,
+                 strategy: str = "auto", **opts):
         import torch
 
         from . import ppsp
@@ -265,7 +266,11 @@ class GpuExecutor:
         self.mode = mode
         self.dist_bits = dist_bits
         self.lane_ctas = lane_ctas
-        self.opts = opts
+        self.opts = dict(opts, strategy=strategy)
+
+    def slot_bytes(self) -> int:
+        """Device bytes of the pair slot each team of a micro-batch holds."""
+        return self.graph.slot_bytes(2, self.dist_bits)
 
     def start(self, pairs: np.ndarray, lane: int):
         """Create the micro-batch's plan and launch it on the lane's stream."""
@@ -297,22 +302,14 @@ class GpuExecutor:
         return status, d
 
 
-def slot_bytes(n: int, searches_per_slot: int, dist_bits: int) -> int:
-    """Device bytes of one team's search memory (distances, two bitmaps, two
-    queues, touched list), as the library sizes it."""
-    flat = max(64, n * searches_per_slot)
-    flat = (flat + 63) // 64 * 64
-    qcap = min(flat, flat // 8 + 4096)
-    tcap = min(flat, flat // 4 + 4096)
-    ocap = max(32 * 256, flat // 4) // 32 * 32
-    return (flat * dist_bits // 8 + 2 * (flat // 8) + 2 * 4 * qcap + 2 * (dist_bits // 8) * qcap + 4 * tcap
-            + ocap * (4 + dist_bits // 8))
-
-
-def memory_model(n: int, lane_ctas: int, dist_bits: int) -> Callable[[np.ndarray], int]:
-    """bytes_for(pairs): every team of the micro-batch holds one pair slot;
-    there are at most min(lane_ctas, queries) teams."""
-    per = slot_bytes(n, 2, dist_bits)
+def memory_model(slot_bytes: int, lane_ctas: int) -> Callable[[np.ndarray], int]:
+    """bytes_for(pairs): the search memory a micro-batch's plan holds.  A
+    plan has at most one team per group and at most lane_ctas teams, and each
+    team holds one slot; with BiD-A* and the AUTO strategy every group has at
+    most two searches, so a pair slot bounds each.  `slot_bytes` is the
+    library's own size of that slot (``Graph.slot_bytes(2, dist_bits)``, i.e.
+    ppsp_slot_bytes), so the model follows the library's capacities."""
+    per = int(slot_bytes)
 
     def f(pairs: np.ndarray) -> int:
         return int(min(lane_ctas, max(1, pairs.shape[0])) * per)

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2506_16488_gb300.serving import (CANCELLED, REJECTED, Request, Scheduler, memory_model, poisson_arrivals,
-                                            serve, slot_bytes)
+                                            serve)
 
 
 def _req(i, k, t=0.0):
@@ -140,11 +140,10 @@ def test_serve_survives_a_failed_micro_batch():
         serve(arrivals[:1], Broken(), Scheduler(lanes=1, max_pairs=4, budget=10, bytes_for=lambda p: 1))
 
 
-def test_memory_model_matches_slot_sizes():
-    f = memory_model(n=1000, lane_ctas=8, dist_bits=64)
-    per = slot_bytes(1000, 2, 64)
-    assert f(np.zeros((3, 2))) == 3 * per and f(np.zeros((100, 2))) == 8 * per
-    assert per >= 2 * 1000 * 8  # at least the two distance arrays
+def test_memory_model_counts_one_slot_per_team():
+    f = memory_model(slot_bytes=12345, lane_ctas=8)
+    assert f(np.zeros((3, 2))) == 3 * 12345 and f(np.zeros((100, 2))) == 8 * 12345
+    assert f(np.zeros((0, 2))) == 12345
 
 
 @pytest.mark.gpu
@@ -164,7 +163,8 @@ def test_serving_results_alone_equal_in_mix():
     with ppsp.Graph.from_csr(g) as G:
         lanes, lane_ctas = 3, 32
         ex = GpuExecutor(G, lanes, mode="bidastar", dist_bits=64, lane_ctas=lane_ctas)
-        sch = Scheduler(lanes, 256, 2 ** 34, memory_model(g.n, lane_ctas, 64))
+        model = memory_model(ex.slot_bytes(), lane_ctas)
+        sch = Scheduler(lanes, 256, 2 ** 34, model)
         out = serve(arrivals, ex, sch)
         assert out["rejected"] == 0
         for r in out["requests"]:
@@ -175,3 +175,38 @@ def test_serving_results_alone_equal_in_mix():
         want = oracle.pairs(g.offsets, g.targets, g.weights, sample)
         got = np.concatenate([r.result for r in out["requests"][:20]])
         assert np.array_equal(got, want)
+
+
+@pytest.mark.gpu
+def test_memory_model_bounds_the_plans_device_memory():
+    """The admission model takes its slot size from the library: every
+    micro-batch plan the executor creates holds at most what the model
+    charges for it (one pair slot per team, teams <= min(lane CTAs, queries))."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2506_16488_gb300 import ppsp
+    from paper_2506_16488_gb300.serving import GpuExecutor
+    from workloads import road_like_graph
+
+    g = road_like_graph(64, seed=91)
+    rng = np.random.default_rng(92)
+    with ppsp.Graph.from_csr(g) as G:
+        lane_ctas = 12
+        ex = GpuExecutor(G, 1, mode="bidastar", dist_bits=64, lane_ctas=lane_ctas)
+        per = ex.slot_bytes()
+        assert per >= 2 * g.n * 8  # at least the two distance arrays
+        assert G.slot_bytes(1, 64) < per <= G.slot_bytes(4, 64)
+        model = memory_model(per, lane_ctas)
+        star = np.stack([np.full(9, g.lcc[0]), g.lcc[1:10]], axis=1)
+        clique = np.array([[a, b] for a in g.lcc[20:26] for b in g.lcc[20:26] if a < b])
+        for pairs in (g.lcc[rng.integers(0, g.lcc.shape[0], size=(k, 2))] for k in (1, 5, 12, 40)):
+            for batch in (pairs, np.concatenate([pairs, star]), np.concatenate([pairs, clique])):
+                plan, out, ev = ex.start(batch.astype(np.uint32), 0)
+                b = plan.device_bytes()
+                assert b["teams"] <= min(lane_ctas, batch.shape[0])
+                assert b["slot_bytes"] <= model(batch), (b, model(batch))
+                ev.synchronize()
+                status, d = ex.poll((plan, out, ev))
+                assert status == 0
+                assert np.array_equal(d, G.batch(batch, mode="bidastar", dist_bits=64))
