@@ -56,19 +56,30 @@ def csr_from_undirected(n: int, u: np.ndarray, v: np.ndarray, w: np.ndarray) -> 
     """Build a symmetric CSR from unique undirected edges (u, v, w), u != v.
 
     Returns (offsets uint64[n+1], targets uint32[m], weights uint32[m]) with
-    each row sorted by target id.
+    each row sorted by target id.  Repeated (u, v) pairs are kept, in input
+    order within their row.
     """
-    u = u.astype(np.uint64)
-    v = v.astype(np.uint64)
+    u = np.asarray(u).astype(np.int64)
+    v = np.asarray(v).astype(np.int64)
     src = np.concatenate([u, v])
     dst = np.concatenate([v, u])
     ww = np.concatenate([w, w]).astype(np.uint32)
-    key = (src << np.uint64(32)) | dst
+    from scipy.sparse import coo_matrix
+
+    # distinct pairs: a counting sort by row, then each row sorted by target
+    # (the same result as sorting the (row, target) keys)
+    a = coo_matrix((ww, (src, dst)), shape=(n, n)).tocsr()
+    a.sort_indices()
+    if a.nnz == src.shape[0]:
+        return a.indptr.astype(np.uint64), a.indices.astype(np.uint32), a.data.astype(np.uint32)
+    # repeated pairs (merged by the conversion above): a stable sort of the
+    # (row, target) keys keeps every copy, in input order
+    key = (src.astype(np.uint64) << np.uint64(32)) | dst.astype(np.uint64)
     order = np.argsort(key, kind="stable")
     src = src[order]
     targets = dst[order].astype(np.uint32)
     weights = ww[order]
-    counts = np.bincount(src.astype(np.int64), minlength=n)
+    counts = np.bincount(src, minlength=n)
     offsets = np.zeros(n + 1, dtype=np.uint64)
     np.cumsum(counts, out=offsets[1:])
     return offsets, targets, weights
@@ -81,7 +92,12 @@ def _dedup_undirected(u, v, w):
     lo = np.minimum(u, v).astype(np.uint64)
     hi = np.maximum(u, v).astype(np.uint64)
     key = (lo << np.uint64(32)) | hi
-    _, first = np.unique(key, return_index=True)
+    # the first copy of each key is its smallest index: an unstable sort,
+    # then the minimum index over each run of equal keys
+    order = np.argsort(key)
+    sk = key[order]
+    starts = np.flatnonzero(np.r_[True, sk[1:] != sk[:-1]])
+    first = np.minimum.reduceat(order, starts)
     first.sort()
     return lo[first], hi[first], w[first]
 
@@ -233,11 +249,12 @@ def rmat_graph(scale: int, seed: int, edge_factor: int = 16, a: float = 0.57, b:
         v = np.zeros(cnt, dtype=np.uint32)
         for level in range(scale):
             r = rng.random(cnt, dtype=np.float32)
-            bit = np.uint32(1 << level)
-            right = ((r >= a) & (r < ab)) | (r >= abc)
+            # quadrant: [0, a) top-left, [a, a+b) top-right, [a+b, a+b+c)
+            # bottom-left, [a+b+c, 1) bottom-right
             down = r >= ab
-            u |= np.where(down, bit, np.uint32(0))
-            v |= np.where(right, bit, np.uint32(0))
+            right = (r >= a) ^ down ^ (r >= abc)
+            u |= down.view(np.uint8).astype(np.uint32) << np.uint32(level)
+            v |= right.view(np.uint8).astype(np.uint32) << np.uint32(level)
         us.append(u)
         vs.append(v)
     u = np.concatenate(us)
