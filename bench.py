@@ -1,10 +1,13 @@
 """Benchmark: exact PPSP queries/sec and GTEPS on one GB300.
 
-Workload (default): the road-like 1024 x 1024 jittered grid (about 1.05 M
-vertices, 10% of grid edges deleted, 0.5% shortcuts of at most 20 cells,
-weights round(1000 * length)) with 1,000 queries split into near/mid/far
-thirds by grid distance, answered with bidirectional A* (Sec. 3.5) as one
-batch (Multi-BiDS schedule, Sec. 4.2).  A step is one pass of the whole batch.
+Workload (default): the largest single-launch configuration, the road-like
+2048 x 2048 jittered grid (about 4.19 M vertices, 10% of grid edges deleted,
+0.5% shortcuts of at most 20 cells, weights round(1000 * length)) with a
+batch of 2,048 queries: 1,552 random pairs and every pair of a 32-vertex
+clique (496 pairs), answered with bidirectional A* (Sec. 3.5) in one
+persistent launch replayed as a CUDA graph.  The launch configuration (batch
+strategy, block size, team size, frontier policy, GetDist rule) is chosen by
+the autotuner at the start of the run; a step is one pass of the whole batch.
 
 Reported:
   value        queries/sec with the graph, the pairs and the output in HBM
@@ -13,9 +16,15 @@ Reported:
   e2e          queries/sec through ppsp_batch with pinned host buffers (query graph
                build, host->device copy of the pairs, search, device->host
                copy of the distances inside the timed region)
-  plain        the same queries one at a time on the whole GPU (Plain-BiDS)
+  plain        the same queries one at a time (Plain-BiDS, best team size)
+  strategies   the paper's Multi-BiDS (Sec. 4.2) and other batch strategies
+               on the same batch
   roofline     algorithmic bytes of the engine kernel per step / step time
   cpu_baseline the CPU Dijkstra oracle on a bounded sample, all host cores
+  config3      RMAT-22 with its three query patterns (BiDS): AUTO, Multi-BiDS,
+               plain, GTEPS and roofline
+  config5      the 4096^2 road-like graph with uint64 distances: a batch of
+               256 queries and the serving loop at 1K, 5K and 20K queries/s
 """
 
 from __future__ import annotations
@@ -120,7 +129,11 @@ def load_workload(cfg: int):
     wl = config_workload(cfg)
     # every batch of the configuration, as one batch (its query graph keeps
     # the random pairs, the star and the clique as separate components)
-    pairs = np.concatenate(list(wl["batches"].values()))
+    names = list(wl["batches"])
+    pairs = np.concatenate([wl["batches"][b] for b in names])
+    # strata of the bounded CPU samples: near/mid/far, or the query patterns
+    wl["labels_all"] = np.asarray(wl["labels"]) if "labels" in wl else np.concatenate(
+        [np.full(wl["batches"][b].shape[0], j, dtype=np.int32) for j, b in enumerate(names)])
     mode = {"bids": "bids", "bidastar": "bidastar", "multi_astar": "bidastar", "serving": "bidastar"}[wl["mode"]]
     return wl, pairs, mode
 
@@ -180,13 +193,14 @@ def read_traffic(workload: str):
     return d.get("dram_bytes_per_launch")
 
 
-def cpu_baseline(g, pairs, labels, budget_s: float = 20.0):
+def cpu_baseline(g, pairs, labels, per_stratum: int = 0):
     import oracle
 
     threads = os.cpu_count() or 1
-    # a bounded, stratified sample: equal numbers of near, mid and far queries
+    # a bounded, stratified sample: equal numbers of queries per stratum
+    # (near/mid/far, or each query pattern)
     rng = np.random.default_rng(7)
-    per = max(1, min(20, threads * 2))
+    per = per_stratum or max(1, min(20, threads * 2))
     idx = np.concatenate([rng.choice(np.nonzero(labels == b)[0], size=min(per, int((labels == b).sum())),
                                      replace=False) for b in np.unique(labels)])
     sample = pairs[idx]
@@ -215,15 +229,15 @@ def run_reference(args):
 
     wl, pairs, mode = load_workload(args.config)
     g = wl["graph"]
-    labels = wl.get("labels", np.zeros(pairs.shape[0], dtype=np.int32))
+    labels = wl["labels_all"]
     threads = os.cpu_count() or 1
     rng = np.random.default_rng(11)
     per = max(1, min(6, threads // 2))
     times = []
     nq = 0
     for step in range(args.warmup + args.steps):
-        idx = np.concatenate([rng.choice(np.nonzero(labels == b)[0], size=per, replace=False)
-                              for b in np.unique(labels)])
+        idx = np.concatenate([rng.choice(np.nonzero(labels == b)[0], size=min(per, int((labels == b).sum())),
+                                         replace=False) for b in np.unique(labels)])
         t0 = time.perf_counter()
         oracle.pairs_threaded(g.offsets, g.targets, g.weights, pairs[idx], threads)
         dt = time.perf_counter() - t0
@@ -247,6 +261,174 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _timed_plan_runs(G, pairs, opts, reps, warmup, stream, flush):
+    """Warm-up and timed runs of one plan (CUDA events on its stream, L2
+    flushed before each timed run); returns (ms list, counters of the last
+    run, distances, plan's group times)."""
+    import torch
+
+    k = pairs.shape[0]
+    out = torch.zeros(k, dtype=torch.int64, device="cuda")
+    plan = G.plan(pairs, stream=stream.cuda_stream, cuda_graph=True, **opts)
+    for _ in range(warmup):
+        plan.run(out.data_ptr())
+        plan.sync()
+    ms, cnt = [], None
+    for i in range(reps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run(out.data_ptr())
+        e1.record(stream)
+        cnt = plan.sync()
+        ms.append(e0.elapsed_time(e1))
+    gms = group_time_stats(plan)
+    plan.close()
+    return ms, cnt, out.cpu().numpy().view(np.uint64).copy(), gms
+
+
+def _plain(G, pairs, got, nq, teams, stream, **popts):
+    """One query at a time (Plain strategy) on a strided subset, best of the
+    given team sizes; answers checked against the batched run's."""
+    import torch
+
+    sel = np.linspace(0, pairs.shape[0] - 1, min(pairs.shape[0], nq)).astype(np.int64)
+    pp_pairs = pairs[sel]
+    kp = pp_pairs.shape[0]
+    runs = []
+    for tc in teams:
+        pp = G.plan(pp_pairs, strategy="plain", stream=stream.cuda_stream, team_ctas=tc, **popts)
+        po = torch.zeros(kp, dtype=torch.int64, device="cuda")
+        pp.run(po.data_ptr())
+        pp.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pp.run(po.data_ptr())
+        e1.record(stream)
+        pc = pp.sync()
+        ms = e0.elapsed_time(e1)
+        assert np.array_equal(po.cpu().numpy().view(np.uint64), got[sel])
+        runs.append({"value": kp / (ms / 1000.0), "unit": "queries/s", "ms": ms, "queries": kp,
+                     "gteps": pc["edges"] / (ms / 1000.0) / 1e9, "rounds": pc["rounds"],
+                     "query_ms": group_time_stats(pp), "team_ctas": tc if tc else "all resident CTAs"})
+        pp.close()
+    best = max(runs, key=lambda r: r["value"])
+    best["tried"] = [{"team_ctas": r["team_ctas"], "value": r["value"]} for r in runs]
+    return best
+
+
+def _roofline(cnt, ms, dist_bytes, astar, peak, peak_kind, traffic=None):
+    alg = algorithmic_bytes(cnt, dist_bytes, astar)
+    achieved = alg / (ms / 1000.0) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": peak_kind, "traffic": traffic, "algorithmic_bytes_per_launch": alg}
+
+
+def _delta_rule(G, mode, args):
+    from paper_2506_16488_gb300 import learned_delta
+
+    if args.delta:
+        return f"fixed {args.delta}", None
+    if args.no_learned:
+        return "default (mean edge weight)", None
+    model = learned_delta.load_model(mode)
+    if model is None:
+        return "default (mean edge weight)", None
+    G.set_delta_model(mode, model)
+    return f"learned MLP ({os.path.relpath(learned_delta.weights_path(mode), ROOT)})", model
+
+
+def _choose_opts(G, pairs, mode, args, world):
+    """Launch configuration of the headline batch: the autotuner's choice
+    (coordinate descent from the AUTO strategy, every trial checked for the
+    same answers) or a fixed strategy."""
+    from paper_2506_16488_gb300 import autotune
+
+    base = {"mode": mode, "strategy": "auto" if args.strategy == "tuned" else args.strategy}
+    if args.delta:
+        base["delta"] = args.delta
+    if args.config == 5:
+        base["dist_bits"] = 64  # the serving graph's configuration keeps uint64 distances
+    if args.strategy != "tuned" or world > 1:
+        return base, None
+    t0 = time.perf_counter()
+    res = autotune.tune(G, pairs, mode, base=base, reps=2, budget_s=args.tune_budget)
+    trials = [{"opts": {k: v for k, v in t["opts"].items() if k not in ("mode", "delta")},
+               "ms": round(t["ms"], 3)} for t in res["trials"]]
+    return res["opts"], {"seconds": time.perf_counter() - t0, "trials": trials,
+                         "chosen": {k: v for k, v in res["opts"].items() if k not in ("mode", "delta")}}
+
+
+def extra_config3(args, peak, peak_kind, flush, stream):
+    """RMAT-22 (power-law shape), its three query patterns in one batch, BiDS:
+    the AUTO strategy, the paper's Multi-BiDS, and plain one at a time."""
+    from paper_2506_16488_gb300 import ppsp
+
+    wl, pairs, mode = load_workload(3)
+    g = wl["graph"]
+    labels = wl["labels_all"]
+    k = pairs.shape[0]
+    res = {"workload": workload_name(3, g, k, mode)}
+    with ppsp.Graph.from_csr(g, with_coords=False) as G:
+        res["delta"], _ = _delta_rule(G, mode, args)
+        ms, cnt, got, gms = _timed_plan_runs(G, pairs, {"mode": mode, "strategy": "auto"}, 3, 1, stream, flush)
+        t = float(np.median(ms))
+        res["auto"] = {"value": k / (t / 1000.0), "unit": "queries/s", "ms": t, "gteps": cnt["edges"] / t / 1e6,
+                       "searches": cnt["searches"], "roofline": _roofline(cnt, t, 4, False, peak, peak_kind),
+                       "group_ms": gms}
+        ms, cnt, got_m, _ = _timed_plan_runs(G, pairs, {"mode": mode, "strategy": "multi"}, 1, 1, stream, flush)
+        assert np.array_equal(got_m, got)
+        res["multi"] = {"value": k / (ms[0] / 1000.0), "unit": "queries/s", "ms": ms[0],
+                        "gteps": cnt["edges"] / ms[0] / 1e6, "searches": cnt["searches"]}
+        res["plain"] = _plain(G, pairs, got, args.plain_queries // 4, [1, 0], stream, mode=mode)
+    res["speedup_vs_plain"] = res["auto"]["value"] / res["plain"]["value"]
+    res["cpu_baseline"] = cpu_baseline(g, pairs, labels, per_stratum=4)
+    return res
+
+
+def extra_config5(args, flush, stream):
+    """The 4096^2 road-like graph with uint64 distances: a batch of 256
+    random queries (AUTO, BiD-A*) and the continuous-batching serving loop."""
+    import torch
+
+    from paper_2506_16488_gb300 import ppsp
+    from paper_2506_16488_gb300.serving import GpuExecutor, Scheduler, memory_model, poisson_arrivals, serve
+
+    wl, pairs, mode = load_workload(5)
+    g = wl["graph"]
+    k = pairs.shape[0]
+    res = {"workload": workload_name(5, g, k, mode) + ", uint64 distances"}
+    with ppsp.Graph.from_csr(g) as G:
+        res["delta"], _ = _delta_rule(G, mode, args)
+        ms, cnt, got, gms = _timed_plan_runs(G, pairs, {"mode": mode, "strategy": "auto", "dist_bits": 64}, 3, 1,
+                                             stream, flush)
+        t = float(np.median(ms))
+        res["batch"] = {"value": k / (t / 1000.0), "unit": "queries/s", "ms": t, "gteps": cnt["edges"] / t / 1e6,
+                        "group_ms": gms}
+        free, _ = torch.cuda.mem_get_info()
+        lanes = args.lanes
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        lane_ctas = args.lane_ctas or max(1, sms // lanes)
+        rng = np.random.default_rng(5003)
+        src = lambda n: g.lcc[rng.integers(0, g.lcc.shape[0], size=(n, 2))]
+        ex = GpuExecutor(G, lanes, mode=mode, dist_bits=64, lane_ctas=lane_ctas, team_ctas=args.team_ctas)
+        model = memory_model(ex.slot_bytes(), lane_ctas)
+        budget = int(0.6 * free)
+        serve(poisson_arrivals(2000, 0.2, src, seed=5004), ex, Scheduler(lanes, 256, budget, model))  # warm-up
+        rates = []
+        for rate in args.rates:
+            out = serve(poisson_arrivals(rate, args.duration, src, seed=int(rate)), ex,
+                        Scheduler(lanes, 256, budget, model))
+            rates.append({"offered_qps": rate, "sustained_qps": out["qps"], "p50_ms": out["latency_p50_ms"],
+                          "p99_ms": out["latency_p99_ms"], "queries": out["queries"],
+                          "requests": len(out["requests"]), "rejected": out["rejected"],
+                          "failed": sum(1 for r in out["requests"] if r.status != 0)})
+        res["serving"] = {"lanes": lanes, "lane_ctas": lane_ctas, "memory_budget_bytes": budget,
+                          "seconds_per_rate": args.duration, "rates": rates}
+    return res
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -267,19 +449,22 @@ def run_ours(args):
 
     wl, pairs, mode = load_workload(args.config)
     g = wl["graph"]
-    labels = wl.get("labels", np.zeros(pairs.shape[0], dtype=np.int32))
+    labels = wl["labels_all"]
     if world > 1 and rank > 0:
         # weak scaling over query-parallel replicas: every rank answers its own
-        # batch of the same shape (near/mid/far mix, same size) on its copy
+        # batch of the same shape (same size and pattern mix) on its copy
         from paper_2506_16488_gb300.replicas import rank_seed
         from workloads import near_mid_far_pairs, random_pairs
 
-        if "labels" in wl:
+        if "labels" in wl and args.config == 2:
             pairs, labels = near_mid_far_pairs(g, pairs.shape[0], rank_seed(args.config * 1000 + 2, rank))
         else:
-            pairs = random_pairs(g, pairs.shape[0], rank_seed(args.config * 1000 + 2, rank))
+            keep = labels != 0  # the patterns (clique, star) stay; the random pairs are redrawn
+            fresh = random_pairs(g, int((labels == 0).sum()), rank_seed(args.config * 1000 + 2, rank))
+            pairs = np.concatenate([fresh, pairs[keep]])
+            labels = np.concatenate([np.zeros(fresh.shape[0], dtype=labels.dtype), labels[keep]])
     if args.queries and args.queries < pairs.shape[0]:
-        # an evenly strided subset keeps the near/mid/far mix
+        # an evenly strided subset keeps the pattern mix
         sel = np.linspace(0, pairs.shape[0] - 1, args.queries).astype(np.int64)
         pairs, labels = pairs[sel], labels[sel]
     k = pairs.shape[0]
@@ -288,29 +473,20 @@ def run_ours(args):
         workload += f", at most {args.max_ctas} CTAs"
     G = ppsp.Graph.from_csr(g)
     stream = torch.cuda.Stream()
-    opts = dict(mode=mode, strategy="multi", stream=stream.cuda_stream, max_ctas=args.max_ctas, cuda_graph=True)
-    delta_rule = "default (mean edge weight)"
-    model = None
-    if args.delta:
-        opts["delta"] = args.delta
-        delta_rule = f"fixed {args.delta}"
-    elif not args.no_learned:
-        from paper_2506_16488_gb300 import learned_delta
-
-        model = learned_delta.load_model(mode)
-        if model is not None:
-            G.set_delta_model(mode, model)
-            delta_rule = f"learned MLP ({os.path.relpath(learned_delta.weights_path(mode), ROOT)})"
-    plan = G.plan(pairs, **opts)
-    out = torch.zeros(k, dtype=torch.int64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    delta_rule, model = _delta_rule(G, mode, args)
+    opts, tuning = _choose_opts(G, pairs, mode, args, world)
+    if args.max_ctas:
+        opts["max_ctas"] = args.max_ctas
+    plan = G.plan(pairs, stream=stream.cuda_stream, cuda_graph=True, **opts)
+    out = torch.zeros(k, dtype=torch.int64, device="cuda")
 
     def step():
         plan.run(out.data_ptr())
 
     for _ in range(args.warmup):
         step()
-        cnt = plan.sync()
+        plan.sync()
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
@@ -339,6 +515,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     got = out.cpu().numpy().view(np.uint64)
+    plan.close()
 
     # e2e through the C ABI with host buffers, in pinned (page-locked)
     # memory as a serving process keeps them (pageable if pinning is refused)
@@ -349,12 +526,12 @@ def run_ours(args):
     except RuntimeError:
         h_pairs = np.ascontiguousarray(pairs, dtype=np.uint32)
         h_res, host_memory = np.zeros(k, dtype=np.uint64), "pageable"
+    bopts = {kk: v for kk, v in opts.items() if kk not in ("mode",)}
     e2e_ms = []
     for i in range(max(1, args.steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = G.batch(h_pairs, out=h_res, mode=mode, strategy="multi",
-                      **({"delta": args.delta} if args.delta else {}))
+        res = G.batch(h_pairs, out=h_res, mode=mode, **bopts)
         e2e_ms.append(1000 * (time.perf_counter() - t0))
     assert np.array_equal(res, got)
     e2e_step_ms = float(np.median(e2e_ms))
@@ -363,83 +540,46 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_step_ms = float(t.item())
 
-    # plain: one query at a time on the whole GPU (Plain-BiDS), with the
-    # default Delta and with the same Delta rule as the batched run
+    # plain: one query at a time (Plain-BiDS), with the default Delta and
+    # with the same Delta rule as the batched run
     default_delta = max(1, int(round(G.info()["w_mean"])))
-
-    # a strided subset keeps the near/mid/far mix and bounds the run time
-    psel = np.linspace(0, k - 1, min(k, args.plain_queries)).astype(np.int64)
-    ppairs = pairs[psel]
-    kp = ppairs.shape[0]
-
-    def run_plain(**popts):
-        pp = G.plan(ppairs, mode=mode, strategy="plain", stream=stream.cuda_stream, **popts)
-        po = torch.zeros(kp, dtype=torch.int64, device="cuda")
-        pp.run(po.data_ptr())
-        pp.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        pp.run(po.data_ptr())
-        e1.record(stream)
-        pc = pp.sync()
-        ms = e0.elapsed_time(e1)
-        assert np.array_equal(po.cpu().numpy().view(np.uint64), got[psel])
-        qms = group_time_stats(pp)
-        pp.close()
-        return {"value": kp / (ms / 1000.0), "unit": "queries/s", "ms": ms, "queries": kp,
-                "gteps": pc["edges"] / (ms / 1000.0) / 1e9, "rounds": pc["rounds"], "query_ms": qms}
-
-    # the plain baseline gets its best team size (fewer CTAs make the
-    # per-step grid barrier cheaper; more give a step more parallelism)
-    def best_plain(**popts):
-        runs = []
-        for tc in args.plain_teams:
-            r = run_plain(team_ctas=tc, **popts)
-            r["team_ctas"] = tc if tc else "all resident CTAs"
-            runs.append(r)
-        best = max(runs, key=lambda r: r["value"])
-        best["tried"] = [{"team_ctas": r["team_ctas"], "value": r["value"]} for r in runs]
-        return best
-
-    # other batch strategies on the same batch (Sec. 4.2 Plain*, Sec. 4.3
-    # Plain-SSSP and VC-SSSP), one timed run each after one untimed run
-    compare = {}
-    for strat in args.compare:
-        copts = dict(mode=mode, strategy=strat, stream=stream.cuda_stream, max_ctas=args.max_ctas)
-        if args.delta:
-            copts["delta"] = args.delta
-        cp = G.plan(pairs, **copts)
-        co = torch.zeros(k, dtype=torch.int64, device="cuda")
-        cp.run(co.data_ptr())
-        cp.sync()
-        with torch.cuda.stream(stream):
-            flush.fill_(7)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        cp.run(co.data_ptr())
-        e1.record(stream)
-        cc = cp.sync()
-        ms = e0.elapsed_time(e1)
-        assert np.array_equal(co.cpu().numpy().view(np.uint64), got), strat
-        cp.close()
-        compare[strat] = {"value": k / (ms / 1000.0), "unit": "queries/s", "ms": ms,
-                          "searches": cc["searches"], "edges": cc["edges"]}
-
-    plain = best_plain(delta=args.delta or default_delta)
+    plain = _plain(G, pairs, got, args.plain_queries, args.plain_teams, stream, mode=mode,
+                   delta=args.delta or default_delta)
     plain["delta"] = f"default {default_delta}" if not args.delta else f"fixed {args.delta}"
-    plain_same = best_plain(**({"delta": args.delta} if args.delta else {}))
+    plain_same = _plain(G, pairs, got, args.plain_queries, args.plain_teams, stream, mode=mode,
+                        **({"delta": args.delta} if args.delta else {}))
     plain_same["delta"] = delta_rule
 
+    # other batch strategies on the same batch (Sec. 4.2 Multi-BiDS, Plain*,
+    # Sec. 4.3 Plain-SSSP and VC-SSSP), one timed run each after one untimed run
+    compare = {}
+    for strat in args.compare:
+        copts = dict(mode=mode, strategy=strat, max_ctas=args.max_ctas)
+        if args.delta:
+            copts["delta"] = args.delta
+        ms, cc, co, _ = _timed_plan_runs(G, pairs, copts, 1, 1, stream, flush)
+        assert np.array_equal(co, got), strat
+        compare[strat] = {"value": k / (ms[0] / 1000.0), "unit": "queries/s", "ms": ms[0],
+                          "searches": cc["searches"], "edges": cc["edges"]}
+    G.close()
+
     if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
         return
     cnt = counters[-1]
     astar = mode in ("bidastar", "astar")
-    alg_bytes = algorithmic_bytes(cnt, 4, astar)
+    dist_bytes = opts.get("dist_bits", 32) // 8
     ms_per_step = total_ms / args.steps
     qps = world * k * args.steps / (total_ms / 1000.0)
     peak, peak_kind = read_peaks()
-    achieved = alg_bytes / (ms_per_step / 1000.0) / 1e9
     cpu = cpu_baseline(g, pairs, labels) if world == 1 else None
+    extras = {}
+    if world == 1:
+        for c in (c for c in args.extras if c != args.config):
+            extras[f"config{c}"] = (extra_config3(args, peak, peak_kind, flush, stream) if c == 3
+                                    else extra_config5(args, flush, stream))
+    chosen = {kk: v for kk, v in opts.items() if kk not in ("mode", "delta", "dist_bits")}
     line = {
         "metric": METRIC,
         "value": qps,
@@ -452,10 +592,11 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "u32",
+        "dtype": "u64" if dist_bytes == 8 else "u32",
         "data": "synthetic",
-        "config": {"workload": workload, "queries_per_step": k, "strategy": "multi (query graph)",
-                   "delta": delta_rule,
+        "config": {"workload": workload, "queries_per_step": k,
+                   "strategy": chosen.get("strategy", "multi"), "launch": chosen,
+                   "tuned": tuning is not None, "delta": delta_rule,
                    "l2": "flushed between steps (256 MB write)",
                    "inputs": "plan (query graph, schedule) built before the timed region; graph, plan and "
                              "output resident in HBM", "parallelism": f"replicas x{world}"},
@@ -469,14 +610,12 @@ def run_ours(args):
         "speedup_vs_plain": qps / world / plain["value"],
         "speedup_vs_plain_same_delta": qps / world / plain_same["value"],
         **({"strategies": compare} if compare else {}),
+        **({"autotune": tuning} if tuning else {}),
         "counters": cnt,
         # per-group device time within the batch (start of its Init to the
         # end of its tidy step on its team)
         "group_ms": group_ms,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": read_traffic(workload),
-                     "algorithmic_bytes_per_launch": alg_bytes},
+        "roofline": _roofline(cnt, ms_per_step, dist_bytes, astar, peak, peak_kind, read_traffic(workload)),
         "e2e": {"value": world * k / (e2e_step_ms / 1000.0), "unit": "queries/s",
                 "h2d_bytes_per_step": int(h_pairs.nbytes), "d2h_bytes_per_step": int(h_res.nbytes),
                 "host_memory": host_memory},
@@ -484,102 +623,43 @@ def run_ours(args):
         "cuda_graph": plan_used_graph,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        **extras,
     }
     print(json.dumps(line), flush=True)
-    plan.close()
-    G.close()
     if world > 1:
         dist.destroy_process_group()
-
-
-def run_serving(args):
-    """Config 5: continuous-batching serving on the 4096^2 road-like graph with
-    uint64 distances; Poisson arrivals of singles and batches of up to 256
-    pairs at several offered rates; p50/p99 latency and sustained queries/s."""
-    import torch
-
-    import __graft_entry__
-
-    __graft_entry__.build()
-    from paper_2506_16488_gb300 import learned_delta, ppsp
-    from paper_2506_16488_gb300.serving import GpuExecutor, Scheduler, memory_model, poisson_arrivals, serve
-    from workloads import config_workload
-
-    wl = config_workload(5, small=args.small)
-    g = wl["graph"]
-    G = ppsp.Graph.from_csr(g)
-    mode = "bidastar"
-    model = None if args.no_learned else learned_delta.load_model(mode)
-    if model is not None:
-        G.set_delta_model(mode, model)
-    free, total = torch.cuda.mem_get_info()
-    budget = int(0.6 * free)
-    # the engine keeps one CTA per SM resident: the lanes split the SMs, and
-    # every query of a micro-batch runs on one CTA (the bucketed one-CTA path)
-    lanes = args.lanes
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    lane_ctas = args.lane_ctas or max(1, sms // lanes)
-    rng = np.random.default_rng(5003)
-    src = lambda k: g.lcc[rng.integers(0, g.lcc.shape[0], size=(k, 2))]
-    ex = GpuExecutor(G, lanes, mode=mode, dist_bits=64, lane_ctas=lane_ctas, team_ctas=args.team_ctas)
-    # warm-up: slot pool and code paths
-    serve(poisson_arrivals(2000, 0.2, src, seed=5004), ex, Scheduler(lanes, 256, budget, memory_model(ex.slot_bytes(), lane_ctas)))
-    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
-    sampler.start()
-    rates = []
-    for rate in args.rates:
-        arr = poisson_arrivals(rate, args.duration, src, seed=int(rate))
-        out = serve(arr, ex, Scheduler(lanes, 256, budget, memory_model(ex.slot_bytes(), lane_ctas)))
-        bad = [r for r in out["requests"] if r.status != 0]
-        rates.append({"offered_qps": rate, "sustained_qps": out["qps"], "p50_ms": out["latency_p50_ms"],
-                      "p99_ms": out["latency_p99_ms"], "queries": out["queries"], "requests": len(arr),
-                      "rejected": out["rejected"], "failed": len(bad)})
-    clocks = sampler.stop()
-    best = max(rates, key=lambda r: r["sustained_qps"] or 0)
-    line = {
-        "metric": "PPSP queries/sec (exact distances) served with continuous batching",
-        "value": best["sustained_qps"], "unit": "queries/s", "n_gpus": 1, "steps": len(rates), "warmup": 1,
-        "ms_per_step": 1000.0 * args.duration, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD_NAMES[5]} ({g.n} vertices, {g.m} CSR entries)", "lanes": lanes,
-                   "lane_ctas": lane_ctas, "team_ctas": args.team_ctas or "auto", "memory_budget_bytes": budget,
-                   "delta": "learned MLP" if model is not None else "default (mean edge weight)"},
-        "rates": rates, "clocks": clocks,
-        "e2e": {"value": best["sustained_qps"], "unit": "queries/s", "h2d_bytes_per_step": None,
-                "d2h_bytes_per_step": None},
-    }
-    print(json.dumps(line), flush=True)
-    G.close()
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=4, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--strategy", default="tuned",
+                    choices=["tuned", "auto", "multi", "plain_star", "vc", "sssp"],
+                    help="batch strategy of the headline run; tuned = autotuner from AUTO")
+    ap.add_argument("--tune-budget", type=float, default=40.0, help="seconds of autotuning (tuned strategy)")
     ap.add_argument("--delta", type=int, default=0)
     ap.add_argument("--no-learned", action="store_true", help="use the default Delta, not the learned model")
     ap.add_argument("--queries", type=int, default=0, help="strided subset of the batch (profiling)")
-    ap.add_argument("--plain-queries", type=int, default=200,
+    ap.add_argument("--plain-queries", type=int, default=100,
                     help="plain baseline: strided subset of the batch, answered one at a time")
-    ap.add_argument("--plain-teams", type=int, nargs="*", default=[1, 16, 64, 0],
+    ap.add_argument("--plain-teams", type=int, nargs="*", default=[1, 16, 0],
                     help="team sizes tried for the plain one-query-at-a-time baseline (0 = all CTAs)")
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on resident CTAs (profiling)")
-    ap.add_argument("--compare", nargs="*", default=[], choices=["plain_star", "sssp", "vc", "auto"],
+    ap.add_argument("--compare", nargs="*", default=["multi"], choices=["multi", "auto", "plain_star", "sssp", "vc"],
                     help="also time these batch strategies on the same batch (one run each)")
-    ap.add_argument("--rates", type=float, nargs="*", default=[1000, 5000, 20000, 50000],
+    ap.add_argument("--extras", type=int, nargs="*", default=[3, 5], choices=[3, 5],
+                    help="also measure these configurations (RMAT-22; the 4096^2 graph with serving)")
+    ap.add_argument("--rates", type=float, nargs="*", default=[1000, 5000, 20000],
                     help="serving (config 5): offered query rates")
     ap.add_argument("--duration", type=float, default=2.0, help="serving (config 5): seconds per rate")
-    ap.add_argument("--small", action="store_true", help="serving (config 5): small graph (tests)")
     ap.add_argument("--lanes", type=int, default=8, help="serving (config 5): concurrent micro-batches")
     ap.add_argument("--lane-ctas", type=int, default=0, help="serving (config 5): CTAs per lane (0 = SMs / lanes)")
     ap.add_argument("--team-ctas", type=int, default=1, help="serving (config 5): CTAs per query (0 = auto)")
     args = ap.parse_args()
-    if args.impl != "reference" and args.config == 5:
-        run_serving(args)
-        return
     if args.impl == "reference":
         run_reference(args)
     else:

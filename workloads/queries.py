@@ -103,7 +103,8 @@ def config_workload(cfg: int, small: bool = False) -> dict:
     if cfg == 4:
         g = road_like_graph(256 if small else 2048, seed=base + 1)
         pairs = np.concatenate([random_pairs(g, 1552, base + 2), clique_pairs(g, 32, base + 3)])
-        return {"graph": g, "batches": {"mixed": pairs}, "mode": "multi_astar"}
+        lab = np.r_[np.zeros(1552, dtype=np.int32), np.ones(496, dtype=np.int32)]  # random pairs, clique
+        return {"graph": g, "batches": {"mixed": pairs}, "labels": lab, "mode": "multi_astar"}
     if cfg == 5:
         g = road_like_graph(256 if small else 4096, seed=base + 1)
         return {"graph": g, "batches": {"random": random_pairs(g, 256, base + 2)}, "mode": "serving"}
