@@ -268,7 +268,8 @@ def _timed_plan_runs(G, pairs, opts, reps, warmup, stream, flush):
     import torch
 
     k = pairs.shape[0]
-    out = torch.zeros(k, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(stream):  # cleared on the stream the plan writes on
+        out = torch.zeros(k, dtype=torch.int64, device="cuda")
     plan = G.plan(pairs, stream=stream.cuda_stream, cuda_graph=True, **opts)
     for _ in range(warmup):
         plan.run(out.data_ptr())
@@ -299,7 +300,8 @@ def _plain(G, pairs, got, nq, teams, stream, **popts):
     runs = []
     for tc in teams:
         pp = G.plan(pp_pairs, strategy="plain", stream=stream.cuda_stream, team_ctas=tc, **popts)
-        po = torch.zeros(kp, dtype=torch.int64, device="cuda")
+        with torch.cuda.stream(stream):
+            po = torch.zeros(kp, dtype=torch.int64, device="cuda")
         pp.run(po.data_ptr())
         pp.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -316,6 +318,10 @@ def _plain(G, pairs, got, nq, teams, stream, **popts):
     best = max(runs, key=lambda r: r["value"])
     best["tried"] = [{"team_ctas": r["team_ctas"], "value": r["value"]} for r in runs]
     return best
+
+
+def ms_per_step_median(step_ms):
+    return float(np.median(step_ms))
 
 
 def _roofline(cnt, ms, dist_bytes, astar, peak, peak_kind, traffic=None):
@@ -406,6 +412,11 @@ def extra_config5(args, flush, stream):
         t = float(np.median(ms))
         res["batch"] = {"value": k / (t / 1000.0), "unit": "queries/s", "ms": t, "gteps": cnt["edges"] / t / 1e6,
                         "group_ms": gms}
+        if args.next2:
+            ms, _, got_m, _ = _timed_plan_runs(G, pairs, {"mode": mode, "strategy": "auto", "dist_bits": 64,
+                                                          "memo_potential": True}, 3, 1, stream, flush)
+            assert np.array_equal(got_m, got)
+            res["batch_memo_potential"] = {"value": k / (float(np.median(ms)) / 1000.0), "ms": float(np.median(ms))}
         free, _ = torch.cuda.mem_get_info()
         lanes = args.lanes
         sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -479,7 +490,8 @@ def run_ours(args):
     if args.max_ctas:
         opts["max_ctas"] = args.max_ctas
     plan = G.plan(pairs, stream=stream.cuda_stream, cuda_graph=True, **opts)
-    out = torch.zeros(k, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(stream):
+        out = torch.zeros(k, dtype=torch.int64, device="cuda")
 
     def step():
         plan.run(out.data_ptr())
@@ -561,6 +573,31 @@ def run_ours(args):
         assert np.array_equal(co, got), strat
         compare[strat] = {"value": k / (ms[0] / 1000.0), "unit": "queries/s", "ms": ms[0],
                           "searches": cc["searches"], "edges": cc["edges"]}
+    # the paper's two implementation optimisations, on and off: heuristic
+    # memoization (Sec. 5) on the headline launch, and pull-then-push
+    # relaxation (App. B) where it applies, on groups run by several CTAs
+    # (the plain one-at-a-time baseline on all CTAs, and Multi-BiDS)
+    next2 = None
+    if args.next2 and world == 1:
+        next2 = {}
+        ms, _, co, _ = _timed_plan_runs(G, pairs, dict(opts, memo_potential=True), 3, 1, stream, flush)
+        assert np.array_equal(co, got)
+        t = float(np.median(ms))
+        next2["memo_potential"] = {"value": k / (t / 1000.0), "ms": t, "off_ms": ms_per_step_median(step_ms)}
+        pl = {}
+        for pull in (False, True):
+            r = _plain(G, pairs, got, args.plain_queries, [0], stream, mode=mode, pull_push=pull)
+            pl["on" if pull else "off"] = {"value": r["value"], "ms": r["ms"], "queries": r["queries"]}
+        next2["pull_push_plain_all_ctas"] = pl
+        ml = {}
+        for pull in (False, True):
+            mopts = dict(mode=mode, strategy="multi", pull_push=pull)
+            if args.delta:
+                mopts["delta"] = args.delta
+            ms, cc, co, _ = _timed_plan_runs(G, pairs, mopts, 1, 1, stream, flush)
+            assert np.array_equal(co, got)
+            ml["on" if pull else "off"] = {"value": k / (ms[0] / 1000.0), "ms": ms[0], "edges": cc["edges"]}
+        next2["pull_push_multi"] = ml
     G.close()
 
     if rank != 0:
@@ -611,6 +648,7 @@ def run_ours(args):
         "speedup_vs_plain_same_delta": qps / world / plain_same["value"],
         **({"strategies": compare} if compare else {}),
         **({"autotune": tuning} if tuning else {}),
+        **({"next2": next2} if next2 else {}),
         "counters": cnt,
         # per-group device time within the batch (start of its Init to the
         # end of its tidy step on its team)
@@ -651,6 +689,8 @@ def main():
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on resident CTAs (profiling)")
     ap.add_argument("--compare", nargs="*", default=["multi"], choices=["multi", "auto", "plain_star", "sssp", "vc"],
                     help="also time these batch strategies on the same batch (one run each)")
+    ap.add_argument("--no-next2", dest="next2", action="store_false",
+                    help="skip the memoization and pull-then-push on/off measurements")
     ap.add_argument("--extras", type=int, nargs="*", default=[3, 5], choices=[3, 5],
                     help="also measure these configurations (RMAT-22; the 4096^2 graph with serving)")
     ap.add_argument("--rates", type=float, nargs="*", default=[1000, 5000, 20000],

@@ -136,7 +136,15 @@ typedef struct {
                                 rho-stepping, which extracts the rho smallest keys; with
                                 Delta huge every step takes the whole frontier, which is
                                 Bellman-Ford).  Groups on several CTAs ignore it.            */
-    uint32_t reserved[5];
+    uint32_t memo_potential; /* 1: heuristic memoization (Sec. 5): the A* potential term of
+                                an entry is computed from the coordinates once per group and
+                                read back from a per-slot array afterwards (4 more bytes per
+                                distance entry of a slot); 0 (default): recomputed each time */
+    uint32_t pull_push;      /* 1: bidirectional relaxation (App. B) on the queue / bitmap
+                                path of undirected graphs: before an extracted vertex pushes,
+                                it pulls min over its neighbours x of d(x) + w(x, u); groups
+                                on one CTA and directed graphs ignore it.  Default 0         */
+    uint32_t reserved[3];
 } ppsp_options;
 
 /* Test hook: device barriers wait for one arrival that never comes, so every

@@ -52,7 +52,7 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     flags = " ".join([nvcc()] + ARCH + NVCC_FLAGS + (extra or []))
     if not os.path.exists(stamp) or open(stamp).read() != flags:
         force = True
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "ppsp.h"))
     srcs = sources()
     objs = []

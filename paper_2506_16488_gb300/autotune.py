@@ -7,7 +7,8 @@ pair team, CTAs per multi-search team,
 the sparse/dense frontier threshold (App. B), the distance layout of
 multi-search groups, the frontier policy, and the GetDist rule of the one-CTA
 path (Delta*-stepping, or rho-stepping / Bellman-Ford by merging buckets,
-Sec. 2).  The tuner runs the batch's plan
+Sec. 2), and the paper's two implementation optimisations (heuristic
+memoization, Sec. 5; pull-then-push relaxation, App. B).  The tuner runs the batch's plan
 with one knob changed at a time (coordinate descent from the library's
 defaults), keeps the fastest setting (minimum of a few device-timed runs),
 checks that every run returns the same distances, and caches the result per
@@ -30,17 +31,19 @@ CACHE = os.path.join(HERE, "tuning", "cache.json")
 
 # the library's defaults (ppsp_options_init), the starting point of the search
 DEFAULTS = {"strategy": "multi", "block_threads": 0, "team_ctas": 0, "big_team_ctas": 0, "dense_den": 0,
-            "layout": "auto", "frontier": "auto", "stepping_rho": 0}
+            "layout": "auto", "frontier": "auto", "stepping_rho": 0, "memo_potential": False, "pull_push": False}
 # knob -> the other values tried, in order
 SPACE = (
     ("strategy", ("auto", "plain_star", "vc")),
     ("block_threads", (1024, 512, 256)),
+    ("memo_potential", (True,)),
+    ("stepping_rho", (256, 1024)),
+    ("pull_push", (True,)),
     ("team_ctas", (1, 2, 4, 8)),
     ("big_team_ctas", (8, 16, 32, 64, 128)),
+    ("frontier", ("sparse",)),
     ("dense_den", (4, 64, 1024)),
     ("layout", ("interleaved", "stacked")),
-    ("frontier", ("sparse",)),
-    ("stepping_rho", (256, 1024)),
 )
 
 
@@ -80,7 +83,8 @@ def tune(G: ppsp.Graph, pairs: np.ndarray, mode: str, base: dict | None = None, 
 
     pairs = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
     stream = torch.cuda.Stream()
-    out = torch.zeros(pairs.shape[0], dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(stream):  # cleared on the stream the plans write on
+        out = torch.zeros(pairs.shape[0], dtype=torch.int64, device="cuda")
     best = dict(base or {})
     best.setdefault("mode", mode)
     best.setdefault("strategy", "multi")

@@ -1,0 +1,15 @@
+// The persistent engine, the general kernel (queue / bitmap path and one-CTA path), for 32-bit tentative
+// distances.
+#include "engine_core.cuh"
+
+namespace ppsp {
+
+ppsp_status launch_engine_u32(const EngineArgs& a, int block_threads, u32 grid, cudaStream_t stream) {
+    return launch_family<u32, false>(a, block_threads, grid, stream);
+}
+
+ppsp_status engine_occupancy_u32(int block_threads, int* bpsm) {
+    return occ_family<u32, false>(block_threads, bpsm);
+}
+
+}  // namespace ppsp

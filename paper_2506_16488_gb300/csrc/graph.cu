@@ -160,9 +160,9 @@ SlotCaps slot_caps(u64 range, int frontier, bool whole_gpu) {
 
 namespace {
 struct SlotLayout {
-    u64 ocap, b_dist, b_bm, b_q, b_fd, b_t, b_st, b_of, b_od, total;
+    u64 ocap, b_dist, b_bm, b_q, b_fd, b_t, b_st, b_of, b_od, b_memo, total;
 };
-SlotLayout slot_layout(int dist_bits, u64 flat_cap, u32 qcap, u32 tcap) {
+SlotLayout slot_layout(int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, bool memo) {
     const u64 W = dist_bits / 8;
     const u64 words = (flat_cap + 31) / 32;
     auto al = [](u64 x) { return (x + 255) & ~255ull; };
@@ -176,28 +176,30 @@ SlotLayout slot_layout(int dist_bits, u64 flat_cap, u32 qcap, u32 tcap) {
     L.b_st = al(sizeof(SlotState));
     L.b_of = al(L.ocap * 4);
     L.b_od = al(L.ocap * W);
-    L.total = L.b_dist + 2 * L.b_bm + 2 * L.b_q + 2 * L.b_fd + L.b_t + L.b_st + L.b_of + L.b_od;
+    L.b_memo = memo ? al(flat_cap * 4) : 0;
+    L.total = L.b_dist + 2 * L.b_bm + 2 * L.b_q + 2 * L.b_fd + L.b_t + L.b_st + L.b_of + L.b_od + L.b_memo;
     return L;
 }
 }  // namespace
 
-u64 slot_alloc_bytes(int dist_bits, u64 flat_cap, u32 qcap, u32 tcap) {
-    return slot_layout(dist_bits, flat_cap, qcap, tcap).total;
+u64 slot_alloc_bytes(int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, bool memo) {
+    return slot_layout(dist_bits, flat_cap, qcap, tcap, memo).total;
 }
 
-ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, Slot** out) {
-    SlotKey key{dist_bits, flat_cap, qcap, tcap};
+ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, bool memo, Slot** out) {
+    SlotKey key{dist_bits, flat_cap, qcap, tcap, memo};
     for (auto it = g->pool.lower_bound(key); it != g->pool.end(); ++it) {
         Slot* s = it->second.get();
         if (!s->busy && it->first.dist_bits == dist_bits && it->first.flat_cap >= flat_cap &&
-            it->first.qcap >= qcap && it->first.tcap >= tcap && it->first.flat_cap <= 2 * flat_cap + 4096) {
+            it->first.qcap >= qcap && it->first.tcap >= tcap && it->first.flat_cap <= 2 * flat_cap + 4096 &&
+            (it->first.memo || !memo)) {
             s->busy = true;
             *out = s;
             return PPSP_OK;
         }
     }
     auto s = std::make_unique<Slot>();
-    const SlotLayout L = slot_layout(dist_bits, flat_cap, qcap, tcap);
+    const SlotLayout L = slot_layout(dist_bits, flat_cap, qcap, tcap, memo);
     const u64 ocap = L.ocap, b_dist = L.b_dist, b_bm = L.b_bm, b_q = L.b_q, b_fd = L.b_fd, b_t = L.b_t,
               b_st = L.b_st, b_of = L.b_of, b_od = L.b_od;
     s->bytes = L.total;
@@ -229,6 +231,8 @@ ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u
     s->dev.touched = (u32*)p;
     p += b_t;
     s->dev.st = (SlotState*)p;
+    p += b_st;
+    s->dev.memo = memo ? (u32*)p : nullptr;
     s->dev.flat_cap = flat_cap;
     s->dev.qcap = qcap;
     s->dev.tcap = tcap;
@@ -238,6 +242,7 @@ ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u
     PPSP_CUDA_TRY(cudaMemset(s->dev.dist, 0xFF, b_dist));
     PPSP_CUDA_TRY(cudaMemset(s->dev.bm[0], 0, 2 * b_bm));
     PPSP_CUDA_TRY(cudaMemset(s->dev.st, 0, b_st));
+    if (memo) PPSP_CUDA_TRY(cudaMemset(s->dev.memo, 0, L.b_memo));  // 0 = no term memoized
     s->busy = true;
     *out = s.get();
     g->pool.emplace(key, std::move(s));
@@ -259,6 +264,7 @@ ppsp_status pool_scrub(ppsp_graph* g, cudaStream_t stream) {
         PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.bm[0], 0, words * 4, stream));
         PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.bm[1], 0, words * 4, stream));
         PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.st, 0, sizeof(SlotState), stream));
+        if (s->dev.memo) PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.memo, 0, s->flat_cap * 4, stream));
     }
     g->pool_dirty = false;
     return PPSP_OK;

@@ -26,9 +26,10 @@ struct SlotKey {
     int dist_bits;
     u64 flat_cap;
     u32 qcap, tcap;
+    bool memo;  // holds the memoized-potential array
     bool operator<(const SlotKey& o) const {
-        return std::tie(dist_bits, flat_cap, qcap, tcap) <
-               std::tie(o.dist_bits, o.flat_cap, o.qcap, o.tcap);
+        return std::tie(dist_bits, flat_cap, qcap, tcap, memo) <
+               std::tie(o.dist_bits, o.flat_cap, o.qcap, o.tcap, o.memo);
     }
 };
 
@@ -81,11 +82,12 @@ struct SlotCaps {
     u32 qcap, tcap;
 };
 SlotCaps slot_caps(u64 range, int frontier, bool whole_gpu);
-// Device bytes of a freshly allocated slot with these capacities.
-u64 slot_alloc_bytes(int dist_bits, u64 flat_cap, u32 qcap, u32 tcap);
+// Device bytes of a freshly allocated slot with these capacities (memo: with
+// the memoized-potential array).
+u64 slot_alloc_bytes(int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, bool memo = false);
 
 // Borrow a slot with at least the requested capacities (allocating if needed).
-ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, Slot** out);
+ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, bool memo, Slot** out);
 void slot_release(ppsp_graph* g, Slot* s);
 // Restore the clean invariant of every pooled slot (after a failed run).
 ppsp_status pool_scrub(ppsp_graph* g, cudaStream_t stream);

@@ -136,6 +136,7 @@ __global__ void na_setup_kernel(unsigned char* base, u32 s, u32 t, u64 m, u64 de
     sd->q[0] = reinterpret_cast<u32*>(base + O_Q0);
     sd->q[1] = reinterpret_cast<u32*>(base + O_Q1);
     sd->touched = reinterpret_cast<u32*>(base + O_TOUCH);
+    sd->memo = nullptr;
     sd->st = reinterpret_cast<SlotState*>(base + O_SLOTST);
     sd->flat_cap = NA_FLAT;
     sd->qcap = NA_QCAP;

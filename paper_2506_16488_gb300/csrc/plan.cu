@@ -20,6 +20,7 @@ struct ppsp_plan {
     int dist_bits = 32;
     int block = 512;
     bool local_only = false;           // every team is one CTA on the bucketed path
+    bool memo = false;                 // slots keep memoized potential terms (Sec. 5)
     u32 grid = 0;
     std::vector<GroupDev> groups;
     std::vector<SearchDev> searches;
@@ -370,6 +371,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     P->stream = (cudaStream_t)o.stream;
     P->dist_bits = o.dist_bits;
     const bool bidir = o.mode == PPSP_BIDS || o.mode == PPSP_BIDASTAR;
+    P->memo = o.memo_potential && g->info.has_coords && (o.mode == PPSP_BIDASTAR || o.mode == PPSP_ASTAR);
     const u64 delta = o.delta ? o.delta : std::max<u64>(1, (u64)std::llround(g->info.w_mean));
     const int strategy = single_query ? PPSP_BATCH_PLAIN : o.batch_strategy;
 
@@ -627,12 +629,20 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
             } else if (o.mode == PPSP_BIDASTAR && G.scnt == 2) {
                 // Sec. 3.5 for an isolated pair: rho_i = h_partner - h_self, so the
                 // two searches use exactly opposite potentials (h_F = -h_B, which
-                // Theorem 3.4 relies on).  Searches of larger query-graph components
-                // run without a potential: a shared search cannot hold the opposite
-                // of every partner's potential at once.
+                // Theorem 3.4 relies on).
                 s.pot = 1;
                 s.pot_b = V[plist[i][0].j];
                 s.key_off = -pot_h_host(g, s.pot_b, s.src);
+            } else if (o.mode == PPSP_BIDASTAR && g->info.has_coords && !plist[i].empty()) {
+                // a shared search cannot hold the opposite of every partner's
+                // potential at once; it takes the smallest partner potential
+                // (multi-target A*), so that for every query (i, j) it prunes
+                // no more than the pair's BiD-A* rule would; the key is shifted
+                // so that the source's key is 0
+                s.pot = 2;
+                i64 hmin = INT64_MAX;
+                for (const PartnerDev& pd : plist[i]) hmin = std::min(hmin, pot_h_host(g, V[pd.j], s.src));
+                s.key_off = -hmin;
             } else if (o.mode == PPSP_ASTAR && !sssp) {
                 s.pot_b = G.target;
                 s.key_off = -pot_h_host(g, G.target, s.src);
@@ -701,50 +711,93 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     struct TeamSpec {
         u32 size, queue;
     };
-    std::vector<TeamSpec> teams;
-    if (strategy == PPSP_BATCH_PLAIN) {
-        // one query (group) at a time on the whole GPU
-        u32 ts = o.team_ctas ? std::min<u32>(grid, (u32)o.team_ctas) : grid;
-        grid = ts;
-        teams.push_back({ts, 1});
-        P->queue_items[1] = big;
-        P->queue_items[1].insert(P->queue_items[1].end(), small.begin(), small.end());
-    } else {
-        double wb = 0, ws = 0;
-        for (u32 gi : big) wb += gwork[gi];
-        for (u32 gi : small) ws += gwork[gi];
-        u32 g_big = 0;
-        if (!big.empty() && small.empty())
-            g_big = grid;
-        else if (!big.empty())
-            g_big = std::min<u32>(grid - 1, std::max<u32>(1, (u32)std::llround(grid * wb / (wb + ws))));
-        u32 tb = 0, nbt = 0;
-        if (g_big) {
-            nbt = std::min<u32>((u32)big.size(), g_big);
-            tb = o.big_team_ctas ? std::min<u32>((u32)o.big_team_ctas, g_big) : g_big / nbt;
-            nbt = std::max<u32>(1, std::min<u32>(g_big / tb, (u32)big.size()));
-            for (u32 t = 0; t < nbt; ++t) teams.push_back({tb, 0});
-        }
-        u32 g_small = grid - nbt * tb;
-        if (!small.empty() && g_small > 0) {
-            // fewer groups than CTAs: give each group a team of several CTAs
-            u32 ts_auto = 1;
-            while (ts_auto * 2 <= 32 && (u64)ts_auto * 2 * small.size() <= g_small) ts_auto *= 2;
-            u32 ts = o.team_ctas ? std::min<u32>((u32)o.team_ctas, g_small) : ts_auto;
-            // no more teams than groups: an idle team would still hold a slot
-            u32 nst = std::max<u32>(1, std::min<u32>(g_small / ts, (u32)small.size()));
-            for (u32 t = 0; t < nst; ++t) teams.push_back({ts, 1});
-            g_small = nst * ts;
+    // teams for `grid` resident CTAs; returns the CTAs they use
+    auto build_teams = [&](u32 grid_in, std::vector<TeamSpec>& teams) -> u32 {
+        teams.clear();
+        u32 g_used = grid_in;
+        if (strategy == PPSP_BATCH_PLAIN) {
+            // one query (group) at a time on the whole GPU
+            u32 ts = o.team_ctas ? std::min<u32>(grid_in, (u32)o.team_ctas) : grid_in;
+            g_used = ts;
+            teams.push_back({ts, 1});
+            P->queue_items[0].clear();
+            P->queue_items[1] = big;
+            P->queue_items[1].insert(P->queue_items[1].end(), small.begin(), small.end());
         } else {
-            g_small = 0;
+            double wb = 0, ws = 0;
+            for (u32 gi : big) wb += gwork[gi];
+            for (u32 gi : small) ws += gwork[gi];
+            u32 g_big = 0;
+            if (!big.empty() && small.empty())
+                g_big = grid_in;
+            else if (!big.empty())
+                g_big = std::min<u32>(grid_in - 1, std::max<u32>(1, (u32)std::llround(grid_in * wb / (wb + ws))));
+            u32 tb = 0, nbt = 0;
+            if (g_big) {
+                nbt = std::min<u32>((u32)big.size(), g_big);
+                tb = o.big_team_ctas ? std::min<u32>((u32)o.big_team_ctas, g_big) : g_big / nbt;
+                nbt = std::max<u32>(1, std::min<u32>(g_big / tb, (u32)big.size()));
+                for (u32 t = 0; t < nbt; ++t) teams.push_back({tb, 0});
+            }
+            u32 g_small = grid_in - nbt * tb;
+            if (!small.empty() && g_small > 0) {
+                // fewer groups than CTAs: give each group a team of several CTAs
+                u32 ts_auto = 1;
+                while (ts_auto * 2 <= 32 && (u64)ts_auto * 2 * small.size() <= g_small) ts_auto *= 2;
+                u32 ts = o.team_ctas ? std::min<u32>((u32)o.team_ctas, g_small) : ts_auto;
+                // no more teams than groups: an idle team would still hold a slot
+                u32 nst = std::max<u32>(1, std::min<u32>(g_small / ts, (u32)small.size()));
+                for (u32 t = 0; t < nst; ++t) teams.push_back({ts, 1});
+                g_small = nst * ts;
+            } else {
+                g_small = 0;
+            }
+            g_used = nbt * tb + g_small;
+            P->queue_items[0] = big;
+            P->queue_items[1] = small;
         }
-        grid = nbt * tb + g_small;
-        P->queue_items[0] = big;
-        P->queue_items[1] = small;
-    }
-    if (teams.empty() || grid == 0) {
-        teams.assign(1, {1, 1});
-        grid = 1;
+        if (teams.empty() || g_used == 0) {
+            teams.assign(1, {1, 1});
+            g_used = 1;
+        }
+        return g_used;
+    };
+    auto all_single = [](const std::vector<TeamSpec>& teams) {
+        bool one = !teams.empty();
+        for (auto& tm : teams) one = one && tm.size == 1;
+        return one;
+    };
+    std::vector<TeamSpec> teams;
+    grid = build_teams(grid, teams);
+
+    // ---- block size ----
+    // Every team of one CTA runs the bucketed shared-memory path, in the
+    // kernel instance without the queue / bitmap path (fewer registers):
+    // by default one CTA of 1,024 threads per SM (one group per CTA then
+    // finishes sooner: on the road benchmark the longest query drops from 34
+    // to 25 ms and the batch from 38.3 to 36.8 ms); block_threads = 512 or
+    // 256 gives two or four CTAs per SM, each running its own group.  Teams
+    // of several CTAs keep 512 threads (128 registers, no spills on the queue
+    // path).  The barrier test hook needs the team barrier, so not with it.
+    if (o.frontier == PPSP_FRONTIER_AUTO && o.debug_flags == 0 && all_single(teams)) {
+        const int lb = o.block_threads ? o.block_threads : 1024;
+        int lbpsm = 0, lsms = 0;
+        if (engine_occupancy(o.dist_bits, lb, &lbpsm, &lsms, true) == PPSP_OK && lbpsm >= 1) {
+            u32 lgrid = (u32)(lbpsm * lsms);
+            if (o.max_ctas > 0) lgrid = std::min<u32>(lgrid, (u32)o.max_ctas);
+            if (lgrid >= grid) {
+                std::vector<TeamSpec> t2;
+                const u32 g2 = build_teams(lgrid, t2);
+                if (all_single(t2)) {
+                    teams.swap(t2);
+                    grid = g2;
+                } else {
+                    build_teams(grid, teams);  // restore the queues of the first layout
+                }
+                P->block = lb;
+                P->local_only = true;
+            }
+        }
     }
     P->grid = grid;
     u32 first = 0;
@@ -754,25 +807,6 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         P->team_queue.push_back(teams[t].queue);
         for (u32 c = 0; c < teams[t].size; ++c) P->cta_team.push_back(t);
         first += teams[t].size;
-    }
-
-    // ---- block size ----
-    // Every team of one CTA runs the bucketed shared-memory path: give it
-    // 1,024 threads when that keeps the same grid co-resident (one group per
-    // CTA then finishes sooner: on the road benchmark the longest query drops
-    // from 34 to 25 ms and the batch from 38.3 to 36.8 ms).  Teams of several
-    // CTAs keep 512 threads (128 registers, no spills on the queue path).
-    if (o.block_threads == 0 && o.frontier == PPSP_FRONTIER_AUTO) {
-        bool all_single = !teams.empty();
-        for (auto& tm : teams) all_single = all_single && tm.size == 1;
-        int bpsm_big = 0, sms_big = 0;
-        if (all_single && engine_occupancy(o.dist_bits, 1024, &bpsm_big, &sms_big) == PPSP_OK &&
-            (u64)bpsm_big * (u64)sms_big >= grid) {
-            P->block = 1024;
-            // the kernel without the queue / bitmap path (fewer registers);
-            // the barrier test hook needs the team barrier, so not with it
-            P->local_only = o.debug_flags == 0;
-        }
     }
 
     // ---- slots ----
@@ -786,7 +820,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     for (u32 t = 0; t < teams.size(); ++t) {
         const SlotCaps sc = slot_caps(range_q[teams[t].queue], o.frontier, teams[t].size == grid);
         Slot* s = nullptr;
-        st = slot_acquire(g, o.dist_bits, sc.flat_cap, sc.qcap, sc.tcap, &s);
+        st = slot_acquire(g, o.dist_bits, sc.flat_cap, sc.qcap, sc.tcap, P->memo, &s);
         if (st != PPSP_OK) {
             for (Slot* x : P->slots) slot_release(g, x);
             return st;
@@ -880,6 +914,8 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     a.dense_den = o.dense_den ? o.dense_den : 16u;
     a.frontier = (u32)o.frontier;
     a.rho = o.stepping_rho;
+    a.memo = P->memo ? 1u : 0u;
+    a.pull = (o.pull_push && g->info.undirected) ? 1u : 0u;
     a.debug = o.debug_flags;
     a.spin_limit = o.spin_limit ? o.spin_limit : (1ull << 26);
     a.err = (u32*)(base + o_err);

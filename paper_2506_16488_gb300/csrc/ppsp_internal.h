@@ -52,7 +52,8 @@ struct GraphDev {
 struct SearchDev {
     u32 src;              // q_i
     u32 pbeg, pcnt;       // partners[pbeg .. pbeg+pcnt)
-    u32 pot;              // 1: bidirectional A* potential rho_i(v) = h_{pot_b}(v) - h_{src}(v)
+    u32 pot;              // 1: bidirectional A* potential rho_i(v) = h_{pot_b}(v) - h_{src}(v);
+                          // 2: multi-target form min_j h_{q_j}(v) - h_{src}(v) over the partners j
     u32 pot_b;            // partner vertex of the potential
     u32 dir;              // 0: searches out-edges (from a source); 1: in-edges (back from a target)
     u32 pad;
@@ -105,6 +106,7 @@ struct SlotDev {
     void* od;             //   and the stored distances
     u32 ocap;             //   split evenly between the ring's buckets
     u32* touched;         // flat indices that left infinity, tcap entries
+    u32* memo;            // memoized potential terms (flat_cap entries, 0 = unset), or null
     SlotState* st;
     u64 flat_cap;         // k_cap * n
     u32 qcap, tcap;
@@ -144,6 +146,8 @@ struct EngineArgs {
     u32 dense_den;        // dense when count > flat_size / dense_den (0 = never)
     u32 frontier;         // PPSP_FRONTIER_*
     u32 rho;              // one-CTA path: a step takes buckets until it holds >= rho entries (0 = one)
+    u32 memo;             // memoize potential terms in the slot (Sec. 5)
+    u32 pull;             // queue / bitmap path: pull before push (App. B), undirected graphs
     u32 debug;
     u64 spin_limit;
     u32* err;
@@ -172,8 +176,10 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
 ppsp_status launch_engine(const EngineArgs& a, int dist_bits, int block_threads, u32 grid,
                           cudaStream_t stream, bool local_only = false);
 
-// Max resident CTAs of the engine for a block size / distance width.
-ppsp_status engine_occupancy(int dist_bits, int block_threads, int* blocks_per_sm, int* sms);
+// Max resident CTAs of the engine for a block size / distance width (of the
+// one-CTA instance when local_only).
+ppsp_status engine_occupancy(int dist_bits, int block_threads, int* blocks_per_sm, int* sms,
+                             bool local_only = false);
 
 // Evaluate potentials h_anchor(v) on the device.
 ppsp_status launch_potential_eval(const GraphDev& g, u32 anchor, const u32* d_verts, u64 count,

@@ -52,7 +52,8 @@ def sweep(G: ppsp.Graph, pairs: np.ndarray, mode: str, grid=GRID, stream=None, r
 
     default = max(1, int(round(G.info()["w_mean"])))
     s = stream or torch.cuda.Stream()
-    out = torch.zeros(pairs.shape[0], dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(s):  # cleared on the stream the plans write on
+        out = torch.zeros(pairs.shape[0], dtype=torch.int64, device="cuda")
     grid = list(grid)
     cols = {}
     state = {"feats": None, "ref": None}

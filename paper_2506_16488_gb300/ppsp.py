@@ -57,7 +57,9 @@ class Options(ctypes.Structure):
         ("debug_flags", ctypes.c_uint32),
         ("cuda_graph", ctypes.c_uint32),
         ("stepping_rho", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 5),
+        ("memo_potential", ctypes.c_uint32),
+        ("pull_push", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 3),
     ]
 
 
@@ -198,7 +200,8 @@ def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, 
                  layout="auto", strategy="multi", block_threads: int = 0, team_ctas: int = 0,
                  big_team_ctas: int = 0, dense_den: int = 0, want_paths: bool = False, max_ctas: int = 0,
                  spin_limit: int = 0, stream: int | None = None, debug_flags: int = 0,
-                 cuda_graph: bool = False, stepping_rho: int = 0) -> Options:
+                 cuda_graph: bool = False, stepping_rho: int = 0, memo_potential: bool = False,
+                 pull_push: bool = False) -> Options:
     """ppsp_options from keyword arguments: the library's defaults
     (ppsp_options_init) overridden by the given values; enum fields accept
     names ("bidastar", "auto", ...) or numbers.  `stream` is a cudaStream_t
@@ -222,6 +225,8 @@ def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, 
     o.debug_flags = debug_flags
     o.cuda_graph = int(bool(cuda_graph))
     o.stepping_rho = stepping_rho
+    o.memo_potential = int(bool(memo_potential))
+    o.pull_push = int(bool(pull_push))
     return o
 
 

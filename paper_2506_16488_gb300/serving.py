@@ -278,7 +278,11 @@ class GpuExecutor:
         plan = self.graph.plan(pairs, mode=self.mode, dist_bits=self.dist_bits, stream=s.cuda_stream,
                                max_ctas=self.lane_ctas, **self.opts)
         try:
-            out = self.torch.zeros(pairs.shape[0], dtype=self.torch.int64, device="cuda")
+            # the output is allocated and cleared on the lane's stream, so the
+            # clear is ordered before the plan's writes (on another stream it
+            # could land after them)
+            with self.torch.cuda.stream(s):
+                out = self.torch.zeros(pairs.shape[0], dtype=self.torch.int64, device="cuda")
             plan.run(out.data_ptr())
         except BaseException:
             plan.close()

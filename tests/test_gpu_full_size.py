@@ -30,7 +30,8 @@ def _run_plan(G, pairs, **opts):
     import torch
 
     stream = torch.cuda.Stream()
-    out = torch.zeros(pairs.shape[0], dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(stream):  # cleared on the stream the plan writes on
+        out = torch.zeros(pairs.shape[0], dtype=torch.int64, device="cuda")
     plan = G.plan(pairs, stream=stream.cuda_stream, cuda_graph=True, **opts)
     for _ in range(2):  # the second run replays the captured graph
         plan.run(out.data_ptr())

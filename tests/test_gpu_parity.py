@@ -375,3 +375,75 @@ def test_large_clique_uncached_partners_and_split():
                 assert np.array_equal(got, want), (size, team)
             if size == 70:
                 assert cnt["groups"] > 1
+
+
+@pytest.mark.parametrize("team", [1, 4])
+def test_multi_target_astar_cliques_and_stars(team):
+    """Multi-BiDS with the multi-target A* potential (each shared search
+    prunes with the smallest partner potential against mumax): exact on
+    cliques, stars and mixed components, on the one-CTA (bucketed) and the
+    multi-CTA (queue / bitmap) paths, and it scans fewer edges than
+    Multi-BiDS without a potential."""
+    g = road_like_graph(120, seed=131)
+    pairs = np.concatenate([clique_pairs(g, 16, 132), star_pairs(g, 20, 133), random_pairs(g, 30, 134)])
+    # a component mixing a clique with pendant pairs
+    pairs = np.concatenate([pairs, np.stack([pairs[:5, 0], random_pairs(g, 5, 135)[:, 1]], axis=1)])
+    want = oracle.pairs(g.offsets, g.targets, g.weights, pairs)
+    with ppsp.Graph.from_csr(g) as G:
+        for delta in (0, 1, 10 ** 7):
+            got, cnt_a = G.batch(pairs, mode="bidastar", strategy="multi", team_ctas=team, big_team_ctas=team,
+                                 delta=delta, return_counters=True)
+            assert np.array_equal(got, want), delta
+        got, cnt_b = G.batch(pairs, mode="bids", strategy="multi", team_ctas=team, big_team_ctas=team,
+                             return_counters=True)
+        assert np.array_equal(got, want)
+        assert cnt_a["edges"] < cnt_b["edges"]
+        for frontier in ("sparse", "dense"):
+            got = G.batch(pairs, mode="bidastar", strategy="multi", frontier=frontier, big_team_ctas=2)
+            assert np.array_equal(got, want), frontier
+
+
+@pytest.mark.parametrize("team", [1, 3])
+def test_memoized_potential(team):
+    """Heuristic memoization (Sec. 5): the potential term of an entry is
+    computed once per group and read back afterwards.  Answers are exact for
+    every plug-in with a potential, on the one-CTA and the queue / bitmap
+    paths, also when the same slots serve the next groups and batches (the
+    memo is cleared with the touched entries)."""
+    g = road_like_graph(140, seed=141)
+    batches = [random_pairs(g, 60, 142), np.concatenate([clique_pairs(g, 9, 143), star_pairs(g, 15, 144)]),
+               near_mid_far_pairs(g, 45, 145)[0]]
+    wants = [oracle.pairs(g.offsets, g.targets, g.weights, b) for b in batches]
+    with ppsp.Graph.from_csr(g) as G:
+        for rep in range(2):
+            for b, want in zip(batches, wants):
+                for mode in ("bidastar", "astar"):
+                    for delta in (0, 1):
+                        got = G.batch(b, mode=mode, memo_potential=True, team_ctas=team, big_team_ctas=team,
+                                      delta=delta)
+                        assert np.array_equal(got, want), (rep, mode, delta)
+        # tiny touched lists force the full reset of the slot (and its memo)
+        for frontier in ("sparse", "dense"):
+            got = G.batch(batches[0], mode="bidastar", memo_potential=True, frontier=frontier, team_ctas=2)
+            assert np.array_equal(got, wants[0]), frontier
+
+
+@pytest.mark.parametrize("team", [2, 8])
+def test_pull_then_push(team):
+    """Bidirectional relaxation (App. B): on the queue / bitmap path an
+    extracted vertex first pulls the best distance over its neighbours, then
+    pushes.  Exact for every plug-in and batch strategy; on a directed graph
+    the option is ignored."""
+    g = road_like_graph(100, seed=151)
+    pairs = np.concatenate([random_pairs(g, 40, 152), clique_pairs(g, 7, 153), star_pairs(g, 10, 154)])
+    want = oracle.pairs(g.offsets, g.targets, g.weights, pairs)
+    with ppsp.Graph.from_csr(g) as G:
+        for mode in ("bids", "bidastar", "et", "astar"):
+            for strategy in ("multi", "plain_star", "vc" if mode in ("bids", "et") else "auto"):
+                for delta in (0, 10 ** 7):
+                    got, cnt = G.batch(pairs, mode=mode, strategy=strategy, pull_push=True, team_ctas=team,
+                                       big_team_ctas=team, delta=delta, return_counters=True)
+                    assert np.array_equal(got, want), (mode, strategy, delta)
+        got = G.batch(pairs, mode="bidastar", pull_push=True, memo_potential=True, frontier="dense",
+                      team_ctas=team)
+        assert np.array_equal(got, want)
