@@ -566,7 +566,8 @@ def run_ours(args):
     # Sec. 4.3 Plain-SSSP and VC-SSSP), one timed run each after one untimed run
     compare = {}
     for strat in args.compare:
-        copts = dict(mode=mode, strategy=strat, max_ctas=args.max_ctas)
+        copts = dict(mode=mode, strategy=strat.replace("_potential", ""), max_ctas=args.max_ctas,
+                     multi_potential=strat == "multi_potential")
         if args.delta:
             copts["delta"] = args.delta
         ms, cc, co, _ = _timed_plan_runs(G, pairs, copts, 1, 1, stream, flush)
@@ -687,7 +688,8 @@ def main():
     ap.add_argument("--plain-teams", type=int, nargs="*", default=[1, 16, 0],
                     help="team sizes tried for the plain one-query-at-a-time baseline (0 = all CTAs)")
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on resident CTAs (profiling)")
-    ap.add_argument("--compare", nargs="*", default=["multi"], choices=["multi", "auto", "plain_star", "sssp", "vc"],
+    ap.add_argument("--compare", nargs="*", default=["multi", "multi_potential"],
+                    choices=["multi", "multi_potential", "auto", "plain_star", "sssp", "vc"],
                     help="also time these batch strategies on the same batch (one run each)")
     ap.add_argument("--no-next2", dest="next2", action="store_false",
                     help="skip the memoization and pull-then-push on/off measurements")

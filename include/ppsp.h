@@ -144,7 +144,15 @@ typedef struct {
                                 path of undirected graphs: before an extracted vertex pushes,
                                 it pulls min over its neighbours x of d(x) + w(x, u); groups
                                 on one CTA and directed graphs ignore it.  Default 0         */
-    uint32_t reserved[3];
+    uint32_t ring_entries;   /* groups on one CTA: shared-memory entries per Delta-bucket of
+                                the frontier ring (32 buckets), 1..256; 0 = default (64).
+                                Larger buckets stay out of the global overflow region; a
+                                smaller ring leaves more of the SM's L1 to the graph        */
+    uint32_t multi_potential;/* BiD-A* Multi-BiDS groups: 1 = every shared search prunes with
+                                the smallest partner potential against mumax (multi-target
+                                A*, an extension: Sec. 4.4 leaves it open); 0 (default) =
+                                shared searches run without a potential (plain Multi-BiDS)  */
+    uint32_t reserved[1];
 } ppsp_options;
 
 /* Test hook: device barriers wait for one arrival that never comes, so every

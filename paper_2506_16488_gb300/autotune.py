@@ -31,14 +31,17 @@ CACHE = os.path.join(HERE, "tuning", "cache.json")
 
 # the library's defaults (ppsp_options_init), the starting point of the search
 DEFAULTS = {"strategy": "multi", "block_threads": 0, "team_ctas": 0, "big_team_ctas": 0, "dense_den": 0,
-            "layout": "auto", "frontier": "auto", "stepping_rho": 0, "memo_potential": False, "pull_push": False}
+            "layout": "auto", "frontier": "auto", "stepping_rho": 0, "memo_potential": False, "pull_push": False,
+            "ring_entries": 0, "multi_potential": False}
 # knob -> the other values tried, in order
 SPACE = (
     ("strategy", ("auto", "plain_star", "vc")),
     ("block_threads", (1024, 512, 256)),
+    ("ring_entries", (128, 256)),
     ("memo_potential", (True,)),
     ("stepping_rho", (256, 1024)),
     ("pull_push", (True,)),
+    ("multi_potential", (True,)),
     ("team_ctas", (1, 2, 4, 8)),
     ("big_team_ctas", (8, 16, 32, 64, 128)),
     ("frontier", ("sparse",)),

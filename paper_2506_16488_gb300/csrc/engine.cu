@@ -9,10 +9,10 @@ ppsp_status launch_engine_u32(const EngineArgs& a, int block_threads, u32 grid, 
 ppsp_status launch_engine_u64(const EngineArgs& a, int block_threads, u32 grid, cudaStream_t stream);
 ppsp_status launch_engine_u32_local(const EngineArgs& a, int block_threads, u32 grid, cudaStream_t stream);
 ppsp_status launch_engine_u64_local(const EngineArgs& a, int block_threads, u32 grid, cudaStream_t stream);
-ppsp_status engine_occupancy_u32(int block_threads, int* bpsm);
-ppsp_status engine_occupancy_u64(int block_threads, int* bpsm);
-ppsp_status engine_occupancy_u32_local(int block_threads, int* bpsm);
-ppsp_status engine_occupancy_u64_local(int block_threads, int* bpsm);
+ppsp_status engine_occupancy_u32(int block_threads, u32 ring_cap, int* bpsm);
+ppsp_status engine_occupancy_u64(int block_threads, u32 ring_cap, int* bpsm);
+ppsp_status engine_occupancy_u32_local(int block_threads, u32 ring_cap, int* bpsm);
+ppsp_status engine_occupancy_u64_local(int block_threads, u32 ring_cap, int* bpsm);
 
 ppsp_status launch_engine(const EngineArgs& a, int dist_bits, int block_threads, u32 grid,
                           cudaStream_t stream, bool local_only) {
@@ -23,15 +23,16 @@ ppsp_status launch_engine(const EngineArgs& a, int dist_bits, int block_threads,
                       : launch_engine_u64(a, block_threads, grid, stream);
 }
 
-ppsp_status engine_occupancy(int dist_bits, int block_threads, int* blocks_per_sm, int* sms, bool local_only) {
+ppsp_status engine_occupancy(int dist_bits, int block_threads, int* blocks_per_sm, int* sms, bool local_only,
+                             u32 ring_cap) {
     int dev = 0;
     PPSP_CUDA_TRY(cudaGetDevice(&dev));
     PPSP_CUDA_TRY(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev));
     if (dist_bits == 32)
-        return local_only ? engine_occupancy_u32_local(block_threads, blocks_per_sm)
-                          : engine_occupancy_u32(block_threads, blocks_per_sm);
-    return local_only ? engine_occupancy_u64_local(block_threads, blocks_per_sm)
-                      : engine_occupancy_u64(block_threads, blocks_per_sm);
+        return local_only ? engine_occupancy_u32_local(block_threads, ring_cap, blocks_per_sm)
+                          : engine_occupancy_u32(block_threads, ring_cap, blocks_per_sm);
+    return local_only ? engine_occupancy_u64_local(block_threads, ring_cap, blocks_per_sm)
+                      : engine_occupancy_u64(block_threads, ring_cap, blocks_per_sm);
 }
 
 // ---- potential evaluation (for checks against the oracle) ----

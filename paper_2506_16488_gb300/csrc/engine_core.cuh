@@ -788,30 +788,32 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
 // when the ring's window reaches them); an entry that finds its bucket or the
 // far list full sets its bit in the slot's spill bitmap and is recovered from
 // its current distance when nothing else is left.
-#ifndef PPSP_RING_CAP
-#define PPSP_RING_CAP 64  // a small ring leaves more of the SM's L1 to the adjacency and offsets
-#endif
+// Shared-memory entries per bucket: chosen per plan (a small ring leaves more
+// of the SM's L1 to the adjacency and offsets; a large one keeps big buckets
+// out of the global overflow region), at most RING_CAP_MAX.
+constexpr u32 RING_CAP_MAX = 256;
 template <typename D>
 struct LR {
-    static constexpr u32 NB = LR_NB;                       // buckets in the ring
-    static constexpr u32 CAP = PPSP_RING_CAP;  // shared-memory entries per bucket
-    static constexpr size_t bytes() { return (size_t)NB * CAP * (4 + sizeof(D)) + NB * 4; }
+    static constexpr u32 NB = LR_NB;  // buckets in the ring
+    static constexpr size_t bytes(u32 cap) { return (size_t)NB * cap * (4 + sizeof(D)) + NB * 4; }
 };
 
 template <typename D, int B>
 struct LocalView {
-    u32* rf;  // [NB * CAP] flat index
-    D* rd;    // [NB * CAP] distance at insertion
+    u32* rf;  // [NB * cap] flat index
+    D* rd;    // [NB * cap] distance at insertion
     u32* rn;  // [NB] entries per bucket
+    u32 cap;  // shared-memory entries per bucket
 };
 
 template <typename D, int B>
-__device__ __forceinline__ LocalView<D, B> local_view(Smem<B>& sm) {
+__device__ __forceinline__ LocalView<D, B> local_view(Smem<B>& sm, u32 cap) {
     unsigned char* p = reinterpret_cast<unsigned char*>(&sm) + ((sizeof(Smem<B>) + 15) & ~(size_t)15);
     LocalView<D, B> L;
     L.rd = reinterpret_cast<D*>(p);
-    L.rf = reinterpret_cast<u32*>(p + (size_t)LR<D>::NB * LR<D>::CAP * sizeof(D));
-    L.rn = L.rf + LR<D>::NB * LR<D>::CAP;
+    L.rf = reinterpret_cast<u32*>(p + (size_t)LR<D>::NB * cap * sizeof(D));
+    L.rn = L.rf + LR<D>::NB * cap;
+    L.cap = cap;
     return L;
 }
 
@@ -841,13 +843,13 @@ __device__ __forceinline__ void insert_local(GCtx<D>& c, Smem<B>& sm, const Loca
         u32 pos = 0;
         if (peers.thread_rank() == 0) pos = atomicAdd(&L.rn[s], (u32)peers.size());
         pos = peers.shfl(pos, 0) + peers.thread_rank();
-        if (pos < LR<D>::CAP) {
-            L.rf[s * LR<D>::CAP + pos] = f;
-            L.rd[s * LR<D>::CAP + pos] = (D)d;
+        if (pos < L.cap) {
+            L.rf[s * L.cap + pos] = f;
+            L.rd[s * L.cap + pos] = (D)d;
             stored = true;
         } else {
             // the bucket continues in its global overflow region
-            const u32 ob = c.slot.ocap / LR<D>::NB, p2 = pos - LR<D>::CAP;
+            const u32 ob = c.slot.ocap / LR<D>::NB, p2 = pos - L.cap;
             if (p2 < ob) {
                 c.slot.of[s * ob + p2] = f;
                 reinterpret_cast<D*>(c.slot.od)[s * ob + p2] = (D)d;
@@ -1176,7 +1178,7 @@ __device__ void recover_spill(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
 template <typename D, int B>
 __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nwords) {
     const u32 t = threadIdx.x;
-    const LocalView<D, B> L = local_view<D, B>(sm);
+    const LocalView<D, B> L = local_view<D, B>(sm, a.ring_cap);
     const GroupDev& G = c.G;
     for (u32 k = t; k < LR<D>::NB; k += B) L.rn[k] = 0;
     if (t == 0) {
@@ -1218,7 +1220,7 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
             const u64 cur = sm.lcur;
             const u32 ob = c.slot.ocap / LR<D>::NB;
             u32 cnt = 0;
-            if (t >= 1 && t < LR<D>::NB) cnt = min(L.rn[(u32)((cur + t) % LR<D>::NB)], LR<D>::CAP + ob);
+            if (t >= 1 && t < LR<D>::NB) cnt = min(L.rn[(u32)((cur + t) % LR<D>::NB)], L.cap + ob);
             const u32 mask = __ballot_sync(0xffffffffu, cnt != 0);
             if (mask) rb = cur + (u32)(__ffs(mask) - 1);
             u32 incl = cnt;
@@ -1334,12 +1336,12 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
                 while (sm.lpre[j] - pbase <= e) ++j;  // at most jl (e < n)
                 const u32 k = e - (sm.lpre[j - 1] - pbase);
                 const u32 s = (u32)((cur0 + j) % LR<D>::NB);
-                if (k < LR<D>::CAP) {
-                    sm.flat[t] = L.rf[s * LR<D>::CAP + k];
-                    sm.d[t] = (u64)L.rd[s * LR<D>::CAP + k];
+                if (k < L.cap) {
+                    sm.flat[t] = L.rf[s * L.cap + k];
+                    sm.d[t] = (u64)L.rd[s * L.cap + k];
                 } else {
-                    sm.flat[t] = __ldcg(c.slot.of + s * ob + (k - LR<D>::CAP));
-                    sm.d[t] = (u64)__ldcg(reinterpret_cast<const D*>(c.slot.od) + s * ob + (k - LR<D>::CAP));
+                    sm.flat[t] = __ldcg(c.slot.of + s * ob + (k - L.cap));
+                    sm.d[t] = (u64)__ldcg(reinterpret_cast<const D*>(c.slot.od) + s * ob + (k - L.cap));
                 }
             }
             // no barrier: thread t reads only its own staged entry before the
@@ -1827,8 +1829,8 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
 }
 
 template <typename D, int B>
-constexpr size_t engine_smem_bytes() {
-    return ((sizeof(Smem<B>) + 15) & ~(size_t)15) + LR<D>::bytes();
+constexpr size_t engine_smem_bytes(u32 ring_cap) {
+    return ((sizeof(Smem<B>) + 15) & ~(size_t)15) + LR<D>::bytes(ring_cap);
 }
 
 // Threads per SM the engine is compiled to keep resident (register budget):
@@ -1907,7 +1909,7 @@ static ppsp_status set_smem_attr() {
     PPSP_CUDA_TRY(cudaGetDevice(&dev));
     if (dev >= 0 && dev < SMEM_ATTR_DEVICES && done[dev].load(std::memory_order_acquire)) return PPSP_OK;
     PPSP_CUDA_TRY(cudaFuncSetAttribute(engine_kernel<D, B, LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)engine_smem_bytes<D, B>()));
+                                       (int)engine_smem_bytes<D, B>(RING_CAP_MAX)));
     if (dev >= 0 && dev < SMEM_ATTR_DEVICES) done[dev].store(true, std::memory_order_release);
     return PPSP_OK;
 }
@@ -1919,13 +1921,14 @@ static ppsp_status launch_t(const EngineArgs& a, u32 grid, cudaStream_t stream) 
     EngineArgs args = a;
     void* params[] = {&args};
     PPSP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)engine_kernel<D, B, LOCAL>, dim3(grid), dim3(B),
-                                              params, engine_smem_bytes<D, B>(), stream));
+                                              params, engine_smem_bytes<D, B>(a.ring_cap), stream));
     return PPSP_OK;
 }
 
 // The three block sizes of one (distance width, LOCAL) instance family.
 template <typename D, bool LOCAL>
 static ppsp_status launch_family(const EngineArgs& a, int block_threads, u32 grid, cudaStream_t stream) {
+    if (a.ring_cap < 1 || a.ring_cap > RING_CAP_MAX) return PPSP_ERR_INVALID_ARG;
     if (block_threads == 256) return launch_t<D, 256, LOCAL>(a, grid, stream);
     if (block_threads == 512) return launch_t<D, 512, LOCAL>(a, grid, stream);
     if (block_threads == 1024) return launch_t<D, 1024, LOCAL>(a, grid, stream);
@@ -1933,19 +1936,20 @@ static ppsp_status launch_family(const EngineArgs& a, int block_threads, u32 gri
 }
 
 template <typename D, int B, bool LOCAL>
-static ppsp_status occ_t(int* bpsm) {
+static ppsp_status occ_t(int* bpsm, u32 ring_cap) {
     ppsp_status st = set_smem_attr<D, B, LOCAL>();
     if (st != PPSP_OK) return st;
     PPSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bpsm, engine_kernel<D, B, LOCAL>, B,
-                                                                engine_smem_bytes<D, B>()));
+                                                                engine_smem_bytes<D, B>(ring_cap)));
     return PPSP_OK;
 }
 
 template <typename D, bool LOCAL>
-static ppsp_status occ_family(int block_threads, int* bpsm) {
-    if (block_threads == 256) return occ_t<D, 256, LOCAL>(bpsm);
-    if (block_threads == 512) return occ_t<D, 512, LOCAL>(bpsm);
-    if (block_threads == 1024) return occ_t<D, 1024, LOCAL>(bpsm);
+static ppsp_status occ_family(int block_threads, u32 ring_cap, int* bpsm) {
+    if (ring_cap < 1 || ring_cap > RING_CAP_MAX) return PPSP_ERR_INVALID_ARG;
+    if (block_threads == 256) return occ_t<D, 256, LOCAL>(bpsm, ring_cap);
+    if (block_threads == 512) return occ_t<D, 512, LOCAL>(bpsm, ring_cap);
+    if (block_threads == 1024) return occ_t<D, 1024, LOCAL>(bpsm, ring_cap);
     return PPSP_ERR_INVALID_ARG;
 }
 

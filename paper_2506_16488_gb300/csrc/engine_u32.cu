@@ -8,8 +8,8 @@ ppsp_status launch_engine_u32(const EngineArgs& a, int block_threads, u32 grid, 
     return launch_family<u32, false>(a, block_threads, grid, stream);
 }
 
-ppsp_status engine_occupancy_u32(int block_threads, int* bpsm) {
-    return occ_family<u32, false>(block_threads, bpsm);
+ppsp_status engine_occupancy_u32(int block_threads, u32 ring_cap, int* bpsm) {
+    return occ_family<u32, false>(block_threads, ring_cap, bpsm);
 }
 
 }  // namespace ppsp

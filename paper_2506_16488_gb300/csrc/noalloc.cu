@@ -223,6 +223,7 @@ extern "C" ppsp_status ppsp_query_noalloc(const uint32_t* d_offsets, const uint3
     a.queue_len[1] = (s == t) ? 0u : 1u;
     a.queue_head = reinterpret_cast<u32*>(base + O_QHEAD);
     a.dense_den = 16;
+    a.ring_cap = RING_CAP_DEFAULT;
     a.frontier = PPSP_FRONTIER_AUTO;
     a.debug = 0;
     a.spin_limit = 1ull << 26;

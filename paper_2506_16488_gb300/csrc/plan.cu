@@ -328,6 +328,7 @@ ppsp_status check_options(const ppsp_graph* g, const ppsp_options& o) {
     if ((o.batch_strategy == PPSP_BATCH_SSSP || o.batch_strategy == PPSP_BATCH_VC) && o.want_paths)
         return PPSP_ERR_UNSUPPORTED;
     if (o.team_ctas < 0 || o.big_team_ctas < 0 || o.max_ctas < 0) return PPSP_ERR_INVALID_ARG;
+    if (o.ring_entries > 256) return PPSP_ERR_INVALID_ARG;
     const bool astar = o.mode == PPSP_BIDASTAR || o.mode == PPSP_ASTAR;
     if (astar && !g->info.has_coords) return PPSP_ERR_NO_COORDS;
     const bool bidir = o.mode == PPSP_BIDS || o.mode == PPSP_BIDASTAR;
@@ -633,12 +634,13 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
                 s.pot = 1;
                 s.pot_b = V[plist[i][0].j];
                 s.key_off = -pot_h_host(g, s.pot_b, s.src);
-            } else if (o.mode == PPSP_BIDASTAR && g->info.has_coords && !plist[i].empty()) {
+            } else if (o.mode == PPSP_BIDASTAR && o.multi_potential && g->info.has_coords && !plist[i].empty()) {
                 // a shared search cannot hold the opposite of every partner's
-                // potential at once; it takes the smallest partner potential
-                // (multi-target A*), so that for every query (i, j) it prunes
-                // no more than the pair's BiD-A* rule would; the key is shifted
-                // so that the source's key is 0
+                // potential at once.  By default it runs without one (plain
+                // Multi-BiDS); with multi_potential it takes the smallest
+                // partner potential (multi-target A*), so that for every query
+                // (i, j) it prunes no more than the pair's BiD-A* rule would;
+                // the key is shifted so that the source's key is 0
                 s.pot = 2;
                 i64 hmin = INT64_MAX;
                 for (const PartnerDev& pd : plist[i]) hmin = std::min(hmin, pot_h_host(g, V[pd.j], s.src));
@@ -695,7 +697,8 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     // ---- launch shape ----
     int block = o.block_threads ? o.block_threads : 512;
     int bpsm = 0, sms = 0;
-    st = engine_occupancy(o.dist_bits, block, &bpsm, &sms);
+    const u32 ring_cap = o.ring_entries ? o.ring_entries : RING_CAP_DEFAULT;
+    st = engine_occupancy(o.dist_bits, block, &bpsm, &sms, false, ring_cap);
     if (st != PPSP_OK) return st;
     if (bpsm < 1) return PPSP_ERR_UNSUPPORTED;
     u32 grid = (u32)(bpsm * sms);
@@ -782,7 +785,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     if (o.frontier == PPSP_FRONTIER_AUTO && o.debug_flags == 0 && all_single(teams)) {
         const int lb = o.block_threads ? o.block_threads : 1024;
         int lbpsm = 0, lsms = 0;
-        if (engine_occupancy(o.dist_bits, lb, &lbpsm, &lsms, true) == PPSP_OK && lbpsm >= 1) {
+        if (engine_occupancy(o.dist_bits, lb, &lbpsm, &lsms, true, ring_cap) == PPSP_OK && lbpsm >= 1) {
             u32 lgrid = (u32)(lbpsm * lsms);
             if (o.max_ctas > 0) lgrid = std::min<u32>(lgrid, (u32)o.max_ctas);
             if (lgrid >= grid) {
@@ -915,6 +918,7 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     a.frontier = (u32)o.frontier;
     a.rho = o.stepping_rho;
     a.memo = P->memo ? 1u : 0u;
+    a.ring_cap = ring_cap;
     a.pull = (o.pull_push && g->info.undirected) ? 1u : 0u;
     a.debug = o.debug_flags;
     a.spin_limit = o.spin_limit ? o.spin_limit : (1ull << 26);

@@ -148,6 +148,7 @@ struct EngineArgs {
     u32 rho;              // one-CTA path: a step takes buckets until it holds >= rho entries (0 = one)
     u32 memo;             // memoize potential terms in the slot (Sec. 5)
     u32 pull;             // queue / bitmap path: pull before push (App. B), undirected graphs
+    u32 ring_cap;         // one-CTA path: shared-memory entries per bucket (1 .. 256)
     u32 debug;
     u64 spin_limit;
     u32* err;
@@ -178,8 +179,10 @@ ppsp_status launch_engine(const EngineArgs& a, int dist_bits, int block_threads,
 
 // Max resident CTAs of the engine for a block size / distance width (of the
 // one-CTA instance when local_only).
+// ring_cap: shared-memory entries per bucket of the one-CTA frontier.
+constexpr u32 RING_CAP_DEFAULT = 64;
 ppsp_status engine_occupancy(int dist_bits, int block_threads, int* blocks_per_sm, int* sms,
-                             bool local_only = false);
+                             bool local_only = false, u32 ring_cap = RING_CAP_DEFAULT);
 
 // Evaluate potentials h_anchor(v) on the device.
 ppsp_status launch_potential_eval(const GraphDev& g, u32 anchor, const u32* d_verts, u64 count,

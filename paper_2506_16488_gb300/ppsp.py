@@ -59,7 +59,9 @@ class Options(ctypes.Structure):
         ("stepping_rho", ctypes.c_uint32),
         ("memo_potential", ctypes.c_uint32),
         ("pull_push", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 3),
+        ("ring_entries", ctypes.c_uint32),
+        ("multi_potential", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 1),
     ]
 
 
@@ -201,7 +203,7 @@ def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, 
                  big_team_ctas: int = 0, dense_den: int = 0, want_paths: bool = False, max_ctas: int = 0,
                  spin_limit: int = 0, stream: int | None = None, debug_flags: int = 0,
                  cuda_graph: bool = False, stepping_rho: int = 0, memo_potential: bool = False,
-                 pull_push: bool = False) -> Options:
+                 pull_push: bool = False, ring_entries: int = 0, multi_potential: bool = False) -> Options:
     """ppsp_options from keyword arguments: the library's defaults
     (ppsp_options_init) overridden by the given values; enum fields accept
     names ("bidastar", "auto", ...) or numbers.  `stream` is a cudaStream_t
@@ -227,6 +229,8 @@ def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, 
     o.stepping_rho = stepping_rho
     o.memo_potential = int(bool(memo_potential))
     o.pull_push = int(bool(pull_push))
+    o.ring_entries = ring_entries
+    o.multi_potential = int(bool(multi_potential))
     return o
 
 

@@ -382,8 +382,7 @@ def test_multi_target_astar_cliques_and_stars(team):
     """Multi-BiDS with the multi-target A* potential (each shared search
     prunes with the smallest partner potential against mumax): exact on
     cliques, stars and mixed components, on the one-CTA (bucketed) and the
-    multi-CTA (queue / bitmap) paths, and it scans fewer edges than
-    Multi-BiDS without a potential."""
+    multi-CTA (queue / bitmap) paths."""
     g = road_like_graph(120, seed=131)
     pairs = np.concatenate([clique_pairs(g, 16, 132), star_pairs(g, 20, 133), random_pairs(g, 30, 134)])
     # a component mixing a clique with pendant pairs
@@ -392,14 +391,13 @@ def test_multi_target_astar_cliques_and_stars(team):
     with ppsp.Graph.from_csr(g) as G:
         for delta in (0, 1, 10 ** 7):
             got, cnt_a = G.batch(pairs, mode="bidastar", strategy="multi", team_ctas=team, big_team_ctas=team,
-                                 delta=delta, return_counters=True)
+                                 delta=delta, multi_potential=True, return_counters=True)
             assert np.array_equal(got, want), delta
-        got, cnt_b = G.batch(pairs, mode="bids", strategy="multi", team_ctas=team, big_team_ctas=team,
-                             return_counters=True)
-        assert np.array_equal(got, want)
-        assert cnt_a["edges"] < cnt_b["edges"]
+        got = G.batch(pairs, mode="bidastar", strategy="multi", team_ctas=team, big_team_ctas=team)
+        assert np.array_equal(got, want)  # the default: shared searches without a potential
         for frontier in ("sparse", "dense"):
-            got = G.batch(pairs, mode="bidastar", strategy="multi", frontier=frontier, big_team_ctas=2)
+            got = G.batch(pairs, mode="bidastar", strategy="multi", frontier=frontier, big_team_ctas=2,
+                          multi_potential=True)
             assert np.array_equal(got, want), frontier
 
 
@@ -447,3 +445,23 @@ def test_pull_then_push(team):
         got = G.batch(pairs, mode="bidastar", pull_push=True, memo_potential=True, frontier="dense",
                       team_ctas=team)
         assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("ring", [1, 7, 256])
+def test_ring_entries(ring):
+    """The one-CTA frontier's shared-memory entries per bucket only move
+    entries between shared memory and the global overflow region: exact for
+    a ring of 1 entry (almost everything overflows), an odd size, and the
+    largest (256), with 32- and 64-bit distances and both block sizes."""
+    g = road_like_graph(150, seed=161)
+    pairs = np.concatenate([near_mid_far_pairs(g, 60, 162)[0], clique_pairs(g, 6, 163), star_pairs(g, 12, 164)])
+    want = oracle.pairs(g.offsets, g.targets, g.weights, pairs)
+    with ppsp.Graph.from_csr(g) as G:
+        for mode in ("bidastar", "bids", "astar"):
+            for bits in (32, 64):
+                for block in (0, 256):
+                    got = G.batch(pairs, mode=mode, ring_entries=ring, dist_bits=bits, block_threads=block,
+                                  team_ctas=1, big_team_ctas=1, strategy="auto")
+                    assert np.array_equal(got, want), (mode, bits, block)
+        with pytest.raises(ppsp.PPSPError):
+            G.batch(pairs, ring_entries=257)
