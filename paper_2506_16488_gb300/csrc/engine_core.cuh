@@ -963,14 +963,57 @@ __device__ __forceinline__ u64 sssp_target_max(const EngineArgs& a, const GCtx<D
     return (all && c.G.qcnt > 0) ? m : INF64;
 }
 
-// mode 0: entries of the current bucket (extract); mode 1: far-list or spill
-// entries (re-bucket, nothing is expanded).  src_f / src_d hold the tile.
+// Entries of a bucket step are spread over the warps: thread (warp w, lane l)
+// takes entry l * (B / 32) + w, so that a step of few entries gives every warp
+// a share and each warp can expand its own entries' edges.
+template <int B>
+__device__ __forceinline__ u32 spread_index(u32 t) {
+    return (t & 31u) * (u32)(B / 32) + (t >> 5);
+}
+
+// A warp expands its own entries' edges while no warp holds more than this
+// many; otherwise the CTA shares the edges (degree scan and owner table).
+constexpr u32 WARP_EDGES_MAX = 256;
+
+// One relaxation of a pair group without waiting for the old distance: the
+// pair just read decides success (a concurrent smaller write only leaves a
+// stale entry behind, which extraction drops).
+template <typename D, int B>
+__device__ __forceinline__ void relax_pair_nowait(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm,
+                                                  const LocalView<D, B>& L, u32 i, u64 d, uint2 ew) {
+    const u32 v2 = ew.x;
+    const u64 nd = d + (u64)ew.y;
+    const PotPre pp = pot_prefetch<D, B>(a, c, sm, v2, 0);  // pair: the term is indexed by vertex
+    u64 x0, x1;
+    ld_pair(c.dist, v2, x0, x1);
+    if (nd > DT<D>::MAXV) {
+        atomicOr(a.err, ERRB_OVERFLOW);
+        return;
+    }
+    const u64 own = i ? x1 : x0, oth = i ? x0 : x1;
+    if (nd >= own) return;
+    const u32 f2 = (v2 << 1) | i;
+    amin_dist(c.dist + f2, nd);
+    ++c.c_r;
+    if (own == DT<D>::INF) touch_local<D, B>(c, sm, f2);
+    if (oth != DT<D>::INF) try_mu(a, c.G, sm, c.G.qbeg, nd + oth);
+    i64 key, pv;
+    key_of<B>(c.G, sm, i, pot_resolve<D, B>(a, c, sm, i, v2, f2, pp), nd, key, pv);
+    if (pruned(pv, sm.bound[i])) return;
+    insert_local<D, B>(c, sm, L, f2, i, key, nd);
+}
+
+// mode 0: entries of the current bucket (extract), spread over the warps
+// (spread_index); mode 1: far-list or spill entries in threads 0 .. cnt - 1
+// (re-bucket, nothing is expanded).  sm.flat / sm.d hold each thread's entry.
 template <typename D, int B>
 __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L, u32 cnt,
                               int mode) {
     const u32 t = threadIdx.x;
     u32 deg = 0;
-    if (t < cnt) {
+    u32 xb0 = 0, xsi = 0;  // the survivor's first edge and search
+    u64 xd = 0;            // and its distance
+    if ((mode == 0 ? spread_index<B>(t) : t) < cnt) {
         const u32 f = sm.flat[t];
         const u64 dins = sm.d[t];  // stored distance (INF: recover from the current one)
         u32 v, i;
@@ -1005,6 +1048,9 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
                     sm.beg[t] = b0;
                     sm.si[t] = (unsigned char)i;
                     sm.d[t] = d;
+                    xb0 = b0;
+                    xsi = i;
+                    xd = d;
                     ++c.c_x;
                 }
             }
@@ -1016,9 +1062,53 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
         return;
     }
     PH_MARK(sm, 1);  // staging + extraction of thread 0's entry
+    // each warp's edges: prefix sums of its lanes' degrees
+    const u32 lane = t & 31u;
+    u32 incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (u32)o) incl += y;
+    }
+    const u32 wtot = __shfl_sync(0xffffffffu, incl, 31);
+    if (!__syncthreads_or(wtot > WARP_EDGES_MAX)) {
+        PH_MARK(sm, 2);  // wait for the slowest extraction
+        // the warp expands its own entries: edge j belongs to the first lane
+        // whose inclusive prefix exceeds j
+        const u32 xex = incl - deg;
+        for (u32 j0 = 0; j0 < wtot; j0 += 32) {
+            const u32 j = j0 + lane;
+            u32 o = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const u32 x = __shfl_sync(0xffffffffu, incl, o + step - 1);
+                if (x <= j) o += step;
+            }
+            const u32 ob0 = __shfl_sync(0xffffffffu, xb0, o);
+            const u32 oex = __shfl_sync(0xffffffffu, xex, o);
+            const u32 osi = __shfl_sync(0xffffffffu, xsi, o);
+            const u32 odl = __shfl_sync(0xffffffffu, (u32)xd, o);
+            const u32 odh = __shfl_sync(0xffffffffu, (u32)(xd >> 32), o);
+            if (j < wtot) {
+                const u64 od = ((u64)odh << 32) | odl;
+                const uint2 ew = __ldg(adj<B>(a, sm, osi) + ob0 + (j - oex));
+                ++c.c_e;
+                if (c.pair)
+                    relax_pair_nowait<D, B>(a, c, sm, L, osi, od, ew);
+                else
+                    relax_local<D, B>(a, c, sm, L, osi, od, ew);
+            }
+        }
+        PH_MARK(sm, 3);  // thread 0's relaxations
+        flush_dir<D, B>(c, sm);
+        __syncthreads();
+        PH_MARK(sm, 4);  // wait for the slowest relaxation
+        return;
+    }
+    // some warp holds many edges (high-degree vertices): the CTA shares them
     u32 total;
     const u32 excl = block_excl_scan<B>(deg, sm, &total, deg > OWN_MAXDEG);
-    sm.pre[t] = (t < cnt) ? excl : total;
+    sm.pre[t] = excl;  // entries are spread over the threads: the prefix covers all of them
     if (deg) write_owner<B>(sm, t, excl, deg);
     __syncthreads();
     PH_MARK(sm, 2);  // scan, including the wait for the slowest extraction
@@ -1040,7 +1130,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
                 nd[k] = DT<D>::INF;
                 si[k] = 0;
                 if (ok[k]) {
-                    const u32 lo = edge_owner<B>(sm, e, cnt);
+                    const u32 lo = edge_owner<B>(sm, e, B);
                     const uint2 ew = __ldg(adj<B>(a, sm, sm.si[lo]) + sm.beg[lo] + (e - sm.pre[lo]));
                     v2[k] = ew.x;
                     si[k] = sm.si[lo];
@@ -1099,7 +1189,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
         }
     } else {
         for (u32 e = t; e < total; e += B) {
-            const u32 lo = edge_owner<B>(sm, e, cnt);
+            const u32 lo = edge_owner<B>(sm, e, B);
             const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
             const uint2 ew = __ldg(adj<B>(a, sm, sm.si[lo]) + edge);
             ++c.c_e;
@@ -1330,8 +1420,8 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
         const u32 n = sm.lpre[jl] - pbase;
         for (u32 base = 0; base < n; base += B) {
             const u32 cnt = min((u32)B, n - base);
-            if (t < cnt) {
-                const u32 e = base + t;
+            if (spread_index<B>(t) < cnt) {
+                const u32 e = base + spread_index<B>(t);
                 u32 j = j0;
                 while (sm.lpre[j] - pbase <= e) ++j;  // at most jl (e < n)
                 const u32 k = e - (sm.lpre[j - 1] - pbase);
