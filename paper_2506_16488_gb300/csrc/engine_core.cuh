@@ -355,12 +355,30 @@ struct GCtx {
     // one-CTA path: this thread's net change of the per-direction entry
     // counts, added to the shared counts once per tile (flush_dir)
     int dc0, dc1;
+    u32* err;         // the device error word (checked builds)
     // heuristic memoization (Sec. 5): the potential term of each entry,
     // stored as term + 2^31 (0 = not evaluated yet), indexed by vertex for
     // pair groups (the two searches' terms are opposite) and by flat index
     // otherwise; null when off
     u32* memo;
 };
+
+// Checked builds (-DPPSP_BOUNDS_CHECK): an index read from memory that falls
+// outside its array records ERRB_INTERNAL with the site number in bits 8..15
+// of the error word, and the access is skipped; normal builds compile the
+// checks out.
+#ifdef PPSP_BOUNDS_CHECK
+__device__ __forceinline__ bool bad_index(const EngineArgs& a, bool ok, u32 site) {
+    if (!ok) atomicOr(a.err, ERRB_INTERNAL | (site << 8));
+    return !ok;
+}
+#else
+__device__ __forceinline__ bool bad_index(const EngineArgs&, bool, u32) { return false; }
+#endif
+
+__device__ __forceinline__ u32 flat_range_of(const GroupDev& G, u32 n) {
+    return G.layout == PPSP_LAYOUT_INTERLEAVED ? (n << G.kshift) : G.scnt * n;
+}
 
 __device__ __forceinline__ u32 flat_of(const GroupDev& G, u32 n, u32 v, u32 i) {
     return G.layout == PPSP_LAYOUT_INTERLEAVED ? ((v << G.kshift) | i) : (i * n + v);
@@ -630,6 +648,7 @@ __device__ __forceinline__ void relax(const EngineArgs& a, GCtx<D>& c, Smem<B>& 
                                       uint2 ew) {
     const u32 v2 = ew.x;
     const u64 nd = d + (u64)ew.y;
+    if (bad_index(a, v2 < c.n, 4)) return;
     // prefetch, overlaps the distance load
     const PotPre pp = pot_prefetch<D, B>(a, c, sm, v2, c.pair ? ((v2 << 1) | i) : flat_of(c.G, c.n, v2, i));
     if (nd > DT<D>::MAXV) {
@@ -686,7 +705,19 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
     u32 deg = 0;
     u32 xf = 0, xv = 0, xi = 0;  // the survivor this thread extracted (pull-then-push)
     u64 xd = DT<D>::INF, xoth = DT<D>::INF;
-    if (t < cnt) {
+    bool valid = t < cnt;
+    if (valid) {
+        u32 v, i;
+        decode_flat(c.G, c.n, sm.flat[t], v, i);
+        if (!(sm.flat[t] < flat_range_of(c.G, c.n) && v < c.n && i < c.G.scnt)) {
+            // an entry of another layout (no search of this group): an
+            // internal error, reported instead of reading past the group's
+            // descriptors
+            atomicOr(a.err, ERRB_INTERNAL | (5u << 8));
+            valid = false;
+        }
+    }
+    if (valid) {
         const u32 f = sm.flat[t];
         u32 v, i;
         decode_flat(c.G, c.n, f, v, i);
@@ -767,6 +798,7 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
     for (u32 e = t; e < total; e += B) {
         const u32 lo = edge_owner<B>(sm, e, cnt);
         const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
+        if (bad_index(a, lo < cnt && edge < a.g.m, 7)) continue;
         const uint2 ew = __ldg(adj<B>(a, sm, sm.si[lo]) + edge);
         ++c.c_e;
         relax<D, B>(a, c, sm, sm.si[lo], sm.d[lo], ew);
@@ -820,6 +852,12 @@ __device__ __forceinline__ LocalView<D, B> local_view(Smem<B>& sm, u32 cap) {
 template <typename D, int B>
 __device__ __forceinline__ void insert_local(GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L, u32 f, u32 i,
                                              i64 key, u64 d) {
+#ifdef PPSP_BOUNDS_CHECK
+    if (f >= flat_range_of(c.G, c.n)) {
+        atomicOr(c.err, ERRB_INTERNAL | (9u << 8));
+        return;
+    }
+#endif
     const u64 step = sm.lstep;
     // b = ceil(key / step), in 32 bits when both fit (the common case)
     u64 b;
@@ -905,6 +943,7 @@ __device__ __forceinline__ void relax_local(const EngineArgs& a, GCtx<D>& c, Sme
                                             u32 i, u64 d, uint2 ew) {
     const u32 v2 = ew.x;
     const u64 nd = d + (u64)ew.y;
+    if (bad_index(a, v2 < c.n, 4)) return;
     const u32 f2 = c.pair ? ((v2 << 1) | i) : flat_of(c.G, c.n, v2, i);
     const PotPre pp = pot_prefetch<D, B>(a, c, sm, v2, f2);
     if (nd > DT<D>::MAXV) {
@@ -983,6 +1022,7 @@ __device__ __forceinline__ void relax_pair_nowait(const EngineArgs& a, GCtx<D>& 
                                                   const LocalView<D, B>& L, u32 i, u64 d, uint2 ew) {
     const u32 v2 = ew.x;
     const u64 nd = d + (u64)ew.y;
+    if (bad_index(a, v2 < c.n, 4)) return;
     const PotPre pp = pot_prefetch<D, B>(a, c, sm, v2, 0);  // pair: the term is indexed by vertex
     u64 x0, x1;
     ld_pair(c.dist, v2, x0, x1);
@@ -1018,6 +1058,14 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
         const u64 dins = sm.d[t];  // stored distance (INF: recover from the current one)
         u32 v, i;
         decode_flat(c.G, c.n, f, v, i);
+        // an entry of another layout (no search of this group): an internal
+        // error, reported instead of reading past the group's descriptors
+        const bool bad = !(f < flat_range_of(c.G, c.n) && v < c.n && i < c.G.scnt);
+        if (bad) {
+            atomicOr(a.err, ERRB_INTERNAL | (2u << 8));
+            v = 0;
+            i = 0;
+        }
         const u32* off = rows<B>(a, sm, i);
         const u32 b0 = __ldg(off + v);
         const u32 b1 = (mode == 0) ? __ldg(off + v + 1) : b0;
@@ -1032,7 +1080,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
             d = ld_dist(c.dist + f);
         }
         if (i) --c.dc1; else --c.dc0;  // the stored entry is consumed
-        if (d != DT<D>::INF && (dins == DT<D>::INF || d == dins)) {
+        if (!bad && d != DT<D>::INF && (dins == DT<D>::INF || d == dins)) {
             i64 key, pv;
             key_of<B>(c.G, sm, i, pot_resolve<D, B>(a, c, sm, i, v, f, pp), d, key, pv);
             if (mode == 1) {
@@ -1089,7 +1137,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
             const u32 osi = __shfl_sync(0xffffffffu, xsi, o);
             const u32 odl = __shfl_sync(0xffffffffu, (u32)xd, o);
             const u32 odh = __shfl_sync(0xffffffffu, (u32)(xd >> 32), o);
-            if (j < wtot) {
+            if (j < wtot && !bad_index(a, ob0 + (j - oex) < a.g.m && osi < c.G.scnt, 3)) {
                 const u64 od = ((u64)odh << 32) | odl;
                 const uint2 ew = __ldg(adj<B>(a, sm, osi) + ob0 + (j - oex));
                 ++c.c_e;
@@ -1131,6 +1179,10 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
                 si[k] = 0;
                 if (ok[k]) {
                     const u32 lo = edge_owner<B>(sm, e, B);
+                    if (bad_index(a, lo < B && sm.beg[lo] + (e - sm.pre[lo]) < a.g.m, 6)) {
+                        ok[k] = false;
+                        continue;
+                    }
                     const uint2 ew = __ldg(adj<B>(a, sm, sm.si[lo]) + sm.beg[lo] + (e - sm.pre[lo]));
                     v2[k] = ew.x;
                     si[k] = sm.si[lo];
@@ -1191,6 +1243,7 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
         for (u32 e = t; e < total; e += B) {
             const u32 lo = edge_owner<B>(sm, e, B);
             const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
+            if (bad_index(a, lo < B && edge < a.g.m, 6)) continue;
             const uint2 ew = __ldg(adj<B>(a, sm, sm.si[lo]) + edge);
             ++c.c_e;
             relax_local<D, B>(a, c, sm, L, sm.si[lo], sm.d[lo], ew);
@@ -1426,7 +1479,10 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
                 while (sm.lpre[j] - pbase <= e) ++j;  // at most jl (e < n)
                 const u32 k = e - (sm.lpre[j - 1] - pbase);
                 const u32 s = (u32)((cur0 + j) % LR<D>::NB);
-                if (k < L.cap) {
+                if (bad_index(a, k < L.cap + ob, 1)) {
+                    sm.flat[t] = 0;
+                    sm.d[t] = 0;
+                } else if (k < L.cap) {
                     sm.flat[t] = L.rf[s * L.cap + k];
                     sm.d[t] = (u64)L.rd[s * L.cap + k];
                 } else {
@@ -1453,6 +1509,11 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
     if (sm.lspill) {
         for (u32 w = t; w < nwords; w += B) c.slot.bm[0][w] = 0u;
     }
+#ifdef PPSP_BOUNDS_CHECK
+    __syncthreads();
+    for (u32 w = t; w < nwords; w += B)
+        if (__ldcg(c.slot.bm[0] + w)) atomicOr(a.err, ERRB_INTERNAL | (21u << 8));
+#endif
     __syncthreads();
     return rounds;
 }
@@ -1588,6 +1649,7 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
     // group cache
     c.pair = (G.mode == GM_BIDIR && G.scnt == 2 && G.layout == PPSP_LAYOUT_INTERLEAVED && G.kshift == 1);
     c.memo = (a.memo && a.g.pc != nullptr) ? slot.memo : nullptr;
+    c.err = a.err;
     if (t == 0) {
         const SearchDev s0 = a.searches[G.sbeg];
         const SearchDev sl = a.searches[G.sbeg + G.scnt - 1];
@@ -1635,6 +1697,22 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
     if (LOCAL && !local) {  // the host chose the local-only kernel for a plan it cannot run
         if (t == 0) atomicOr(a.err, ERRB_INTERNAL);
         return false;
+    }
+    if (!LOCAL && !local) {
+        // the queue / bitmap path reads its two bitmaps as the frontier and as
+        // the dedup of the next one: they start empty over the group's range
+        // whatever an earlier group that used the slot left behind (a word
+        // of another layout decodes to another search)
+        const u32 nwg = (flat_range_of(G, c.n) + 31u) >> 5;
+#ifdef PPSP_BOUNDS_CHECK
+        for (u32 w = tc.rank * B + t; w < nwg; w += tc.size * B)
+            if (__ldcg(slot.bm[0] + w) | __ldcg(slot.bm[1] + w)) atomicOr(a.err, ERRB_INTERNAL | (20u << 8));
+#endif
+        for (u32 w = tc.rank * B + t; w < nwg; w += tc.size * B) {
+            slot.bm[0][w] = 0u;
+            slot.bm[1][w] = 0u;
+        }
+        if (!team_sync(tc, a, &sm.flag)) return false;
     }
     if (tc.rank == 0) {
         if (t < G.scnt) {
@@ -1896,6 +1974,7 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
         } else {
             for (u32 k = tc.rank * B + t; k < tn; k += tc.size * B) {
                 const u32 f = __ldcg(slot.touched + k);
+                if (bad_index(a, f < flat_range && k < slot.tcap, 8)) continue;
                 st_dist(c.dist + f, DT<D>::INF);
                 if (c.memo) c.memo[c.pair ? (f >> 1) : f] = 0u;
             }
@@ -1949,6 +2028,10 @@ __global__ void __launch_bounds__(B, (EngineMinBlocks<B, LOCAL>::value))
     tc.rank = blockIdx.x - a.team_first[tc.team];
     tc.size = a.team_size[tc.team];
     tc.ts = a.tstate + tc.team;
+    if (tc.rank >= tc.size) {  // a CTA outside its team's range: the host's team tables disagree with the grid
+        if (threadIdx.x == 0) atomicOr(a.err, ERRB_INTERNAL);
+        return;
+    }
     const bool never = (a.debug & PPSP_DEBUG_BARRIER_NEVER_RELEASES) != 0;
     tc.global_bar = tc.size > 1 || never;
     tc.expect = tc.size + (never ? 1u : 0u);

@@ -1,4 +1,5 @@
 // Graph creation, validation, A* potential, slot pool, small ABI helpers.
+#include <cstdarg>
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -15,6 +16,20 @@ static thread_local char g_last_error[512] = {0};
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
     snprintf(g_last_error, sizeof(g_last_error), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file,
              line);
+}
+
+void set_last_device_error(u32 err) {
+    snprintf(g_last_error, sizeof(g_last_error), "device error word 0x%x (internal error, site %u)", err,
+             (err >> 8) & 0xFFu);
+}
+
+void set_last_internal_error(const char* fmt, ...) {
+    char msg[400];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof(msg), fmt, ap);
+    va_end(ap);
+    snprintf(g_last_error, sizeof(g_last_error), "internal error: %s", msg);
 }
 
 u64 isqrt_host(u64 x) {
@@ -186,7 +201,8 @@ u64 slot_alloc_bytes(int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, bool memo)
     return slot_layout(dist_bits, flat_cap, qcap, tcap, memo).total;
 }
 
-ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, bool memo, Slot** out) {
+ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, bool memo,
+                         cudaStream_t stream, Slot** out) {
     SlotKey key{dist_bits, flat_cap, qcap, tcap, memo};
     for (auto it = g->pool.lower_bound(key); it != g->pool.end(); ++it) {
         Slot* s = it->second.get();
@@ -238,11 +254,14 @@ ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u
     s->dev.tcap = tcap;
     s->dist_bits = dist_bits;
     s->flat_cap = flat_cap;
-    // clean invariant: distances infinite (all-ones bytes), bitmaps zero
-    PPSP_CUDA_TRY(cudaMemset(s->dev.dist, 0xFF, b_dist));
-    PPSP_CUDA_TRY(cudaMemset(s->dev.bm[0], 0, 2 * b_bm));
-    PPSP_CUDA_TRY(cudaMemset(s->dev.st, 0, b_st));
-    if (memo) PPSP_CUDA_TRY(cudaMemset(s->dev.memo, 0, L.b_memo));  // 0 = no term memoized
+    // clean invariant: distances infinite (all-ones bytes), bitmaps zero.
+    // Written on the stream of the plan that takes the slot, so the writes
+    // are ordered before its searches (a plain cudaMemset runs on the legacy
+    // default stream, which a non-blocking stream does not wait for).
+    PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.dist, 0xFF, b_dist, stream));
+    PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.bm[0], 0, 2 * b_bm, stream));
+    PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.st, 0, b_st, stream));
+    if (memo) PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.memo, 0, L.b_memo, stream));  // 0 = no term memoized
     s->busy = true;
     *out = s.get();
     g->pool.emplace(key, std::move(s));
@@ -254,19 +273,16 @@ void slot_release(ppsp_graph* g, Slot* s) {
     if (s) s->busy = false;
 }
 
-ppsp_status pool_scrub(ppsp_graph* g, cudaStream_t stream) {
-    if (!g->pool_dirty) return PPSP_OK;
-    for (auto& kv : g->pool) {
-        Slot* s = kv.second.get();
-        const u64 W = s->dist_bits / 8;
-        const u64 words = (s->flat_cap + 31) / 32;
-        PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.dist, 0xFF, s->flat_cap * W, stream));
-        PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.bm[0], 0, words * 4, stream));
-        PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.bm[1], 0, words * 4, stream));
-        PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.st, 0, sizeof(SlotState), stream));
-        if (s->dev.memo) PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.memo, 0, s->flat_cap * 4, stream));
-    }
-    g->pool_dirty = false;
+ppsp_status slot_scrub(Slot* s, cudaStream_t stream) {
+    if (!s->dirty) return PPSP_OK;
+    const u64 W = s->dist_bits / 8;
+    const u64 words = (s->flat_cap + 31) / 32;
+    PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.dist, 0xFF, s->flat_cap * W, stream));
+    PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.bm[0], 0, words * 4, stream));
+    PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.bm[1], 0, words * 4, stream));
+    PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.st, 0, sizeof(SlotState), stream));
+    if (s->dev.memo) PPSP_CUDA_TRY(cudaMemsetAsync(s->dev.memo, 0, s->flat_cap * 4, stream));
+    s->dirty = false;
     return PPSP_OK;
 }
 

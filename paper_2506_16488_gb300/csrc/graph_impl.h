@@ -20,6 +20,7 @@ struct Slot {
     int dist_bits = 32;
     u64 flat_cap = 0;
     bool busy = false;
+    bool dirty = false;  // a failed run may have left it unclean: scrub before its next use
 };
 
 struct SlotKey {
@@ -50,7 +51,6 @@ struct ppsp_graph {
     std::vector<uint64_t> deg;     // host copy of degrees (features, schedules)
     // slot pool
     std::multimap<ppsp::SlotKey, std::unique_ptr<ppsp::Slot>> pool;
-    bool pool_dirty = false;
     std::mutex mu;
     // scratch for small transfers (potential eval)
     ppsp::u32* d_scratch_u32 = nullptr;
@@ -68,6 +68,8 @@ struct ppsp_graph {
         g.pc = d_pc;
         g.n = (ppsp::u32)n;
         g.pot_shift = (ppsp::u32)pot_shift;
+        g.m = (ppsp::u32)m;
+        g.pad = 0;
         return g;
     }
 };
@@ -86,11 +88,14 @@ SlotCaps slot_caps(u64 range, int frontier, bool whole_gpu);
 // the memoized-potential array).
 u64 slot_alloc_bytes(int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, bool memo = false);
 
-// Borrow a slot with at least the requested capacities (allocating if needed).
-ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, bool memo, Slot** out);
+// Borrow a slot with at least the requested capacities (allocating if needed;
+// a new slot is initialised on `stream`, the stream of the plan that takes it).
+ppsp_status slot_acquire(ppsp_graph* g, int dist_bits, u64 flat_cap, u32 qcap, u32 tcap, bool memo,
+                         cudaStream_t stream, Slot** out);
 void slot_release(ppsp_graph* g, Slot* s);
-// Restore the clean invariant of every pooled slot (after a failed run).
-ppsp_status pool_scrub(ppsp_graph* g, cudaStream_t stream);
+// Restore the clean invariant of a slot a failed run used, on the stream of
+// the plan that uses it next (other plans' slots are left alone).
+ppsp_status slot_scrub(Slot* s, cudaStream_t stream);
 
 // Exact floor(sqrt(x)) on the host.
 u64 isqrt_host(u64 x);

@@ -205,6 +205,7 @@ extern "C" ppsp_status ppsp_query_noalloc(const uint32_t* d_offsets, const uint3
     a.g.pc = nullptr;
     a.g.n = n;
     a.g.pot_shift = 0;
+    a.g.m = (u32)m;
     a.groups = reinterpret_cast<const GroupDev*>(base + O_GROUP);
     a.searches = reinterpret_cast<const SearchDev*>(base + O_SEARCH);
     a.partners = reinterpret_cast<const PartnerDev*>(base + O_PART);

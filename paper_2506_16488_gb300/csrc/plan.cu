@@ -338,6 +338,8 @@ ppsp_status check_options(const ppsp_graph* g, const ppsp_options& o) {
 }  // namespace
 
 static void plan_free_partial(ppsp_plan* P) {
+    // a new slot may still be initialising on the plan's stream
+    cudaStreamSynchronize(P->stream);
     for (Slot* x : P->slots) slot_release(P->g, x);
     P->slots.clear();
     // stream-ordered frees: no device-wide synchronisation, so plans on other
@@ -771,7 +773,8 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         return one;
     };
     std::vector<TeamSpec> teams;
-    grid = build_teams(grid, teams);
+    const u32 grid_max = grid;  // resident CTAs of the general kernel
+    grid = build_teams(grid_max, teams);
 
     // ---- block size ----
     // Every team of one CTA runs the bucketed shared-memory path, in the
@@ -795,7 +798,9 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
                     teams.swap(t2);
                     grid = g2;
                 } else {
-                    build_teams(grid, teams);  // restore the queues of the first layout
+                    // the first layout (all single), rebuilt from the same
+                    // input so that its queues are restored with it
+                    grid = build_teams(grid_max, teams);
                 }
                 P->block = lb;
                 P->local_only = true;
@@ -811,6 +816,12 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
         for (u32 c = 0; c < teams[t].size; ++c) P->cta_team.push_back(t);
         first += teams[t].size;
     }
+    // every launched CTA belongs to exactly one team (a CTA without one would
+    // read past the team tables)
+    if (first != grid || grid == 0) {
+        set_last_internal_error("team layout covers %u CTAs of a grid of %u", first, grid);
+        return PPSP_ERR_CUDA;
+    }
 
     // ---- slots ----
     u64 range_q[MAX_QUEUES] = {0, 0};
@@ -823,8 +834,10 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     for (u32 t = 0; t < teams.size(); ++t) {
         const SlotCaps sc = slot_caps(range_q[teams[t].queue], o.frontier, teams[t].size == grid);
         Slot* s = nullptr;
-        st = slot_acquire(g, o.dist_bits, sc.flat_cap, sc.qcap, sc.tcap, P->memo, &s);
+        st = slot_acquire(g, o.dist_bits, sc.flat_cap, sc.qcap, sc.tcap, P->memo, P->stream, &s);
         if (st != PPSP_OK) {
+            cudaStreamSynchronize(P->stream);  // new slots may still be initialising
+            cudaGetLastError();
             for (Slot* x : P->slots) slot_release(g, x);
             return st;
         }
@@ -863,6 +876,8 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     P->arena_bytes = off;
     cudaError_t ce = cudaMallocAsync(&P->d_arena, P->arena_bytes, P->stream);
     if (ce != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamSynchronize(P->stream);  // new slots may still be initialising
         cudaGetLastError();
         for (Slot* x : P->slots) slot_release(g, x);
         return ce == cudaErrorMemoryAllocation ? PPSP_ERR_OOM : PPSP_ERR_CUDA;
@@ -984,7 +999,9 @@ static ppsp_status plan_launch_direct(ppsp_plan* P, u64* d_out);
 // and replay it; any capture failure falls back to direct launches.
 static ppsp_status plan_launch(ppsp_plan* P, u64* d_out) {
     P->last_used_graph = false;
-    if (!P->opt.cuda_graph || P->stream == nullptr || P->graph_failed || P->g->pool_dirty)
+    bool dirty = false;
+    for (const Slot* s : P->slots) dirty = dirty || s->dirty;
+    if (!P->opt.cuda_graph || P->stream == nullptr || P->graph_failed || dirty)
         return plan_launch_direct(P, d_out);
     if (P->gexec == nullptr || P->gexec_out != d_out) {
         if (P->gexec) {
@@ -1022,8 +1039,11 @@ static ppsp_status plan_launch(ppsp_plan* P, u64* d_out) {
 }
 
 static ppsp_status plan_launch_direct(ppsp_plan* P, u64* d_out) {
-    ppsp_status st = pool_scrub(P->g, P->stream);
-    if (st != PPSP_OK) return st;
+    for (Slot* s : P->slots) {
+        ppsp_status st = slot_scrub(s, P->stream);
+        if (st != PPSP_OK) return st;
+    }
+    ppsp_status st = PPSP_OK;
     PPSP_CUDA_TRY(cudaMemsetAsync(P->d_runstate, 0, P->runstate_bytes, P->stream));
     if (P->paths && !P->qedges.empty())
         PPSP_CUDA_TRY(cudaMemsetAsync(P->d_meet, 0xFF, P->qedges.size() * 4, P->stream));
@@ -1069,9 +1089,10 @@ static ppsp_status plan_wait(ppsp_plan* P, ppsp_counters* counters) {
         counters->dense_rounds = ec.dense_rounds;
     }
     if (err) {
-        P->g->pool_dirty = true;
+        for (Slot* s : P->slots) s->dirty = true;
         if (err & ERRB_OVERFLOW) return PPSP_ERR_OVERFLOW;
         if (err & ERRB_TIMEOUT) return PPSP_ERR_TIMEOUT;
+        set_last_device_error(err);
         return PPSP_ERR_CUDA;
     }
     return PPSP_OK;

@@ -47,6 +47,8 @@ struct GraphDev {
     const int2* pc;       // [n] integer potential coordinates, or null
     u32 n;
     u32 pot_shift;        // F: h = isqrt(d2 >> 2F)
+    u32 m;                // adjacency entries (bounds of checked builds)
+    u32 pad;
 };
 
 struct SearchDev {
@@ -172,6 +174,10 @@ struct EngineArgs {
     } while (0)
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+// Detail text for an internal device error (the error word).
+void set_last_device_error(u32 err);
+// Detail text for an internal host-side inconsistency (printf format).
+void set_last_internal_error(const char* fmt, ...);
 
 // Launch the persistent engine.  dist_bits selects the distance width.
 ppsp_status launch_engine(const EngineArgs& a, int dist_bits, int block_threads, u32 grid,

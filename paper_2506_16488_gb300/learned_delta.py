@@ -119,6 +119,20 @@ def regret(times: np.ndarray, y_pred: np.ndarray, grid=GRID) -> float:
     return float(chosen / times.min(axis=1).sum() - 1.0)
 
 
+def doubling_regret(times: np.ndarray, grid=GRID):
+    """Regret of the paper's rule (Sec. 6.1): one Delta for the whole graph,
+    found by doubling until the time stops improving -- here the grid point
+    with the smallest total time over the swept points (the sweep walks the
+    grid the same way, so it visits the rule's choice).  Returns (regret,
+    chosen grid point)."""
+    ok = _finite_cols(times)
+    if not ok.any():
+        return None, None
+    tot = times[:, ok].sum(axis=0)
+    j = int(np.argmin(tot))
+    return float(tot[j] / times.min(axis=1).sum() - 1.0), int(np.asarray(grid)[ok][j])
+
+
 def default_regret(times: np.ndarray, grid=GRID):
     """Regret of the default increment, or None when the sweep never timed it."""
     j0 = list(grid).index(0)
@@ -184,8 +198,10 @@ def _training_sets(mode: str, build: bool = True):
         return [(n, None, None, st) for n, st in names]
     # (name, graph, pairs, first grid point of the sweep)
     sets = []
-    g = road_like_graph(1024, seed=2001)  # the road-like benchmark graph, other queries
-    p, _ = near_mid_far_pairs(g, 1000, seed=2777)
+    # a 1024^2 road-like graph of its own seed (the benchmark graphs of every
+    # size are held out for evaluation)
+    g = road_like_graph(1024, seed=9601)
+    p, _ = near_mid_far_pairs(g, 1000, seed=9602)
     sets.append(("road1024", g, p, 0))
     g = road_like_graph(512, seed=9001)
     p, _ = near_mid_far_pairs(g, 600, seed=9002)
@@ -268,6 +284,7 @@ def build_and_train(mode: str, out_dir: str = WEIGHTS_DIR, epochs: int = 600, lo
     for i, t in enumerate(times_all):
         meta_sets[i]["regret_learned"] = regret(t, pred[offs[i]:offs[i + 1]] - margin)
         meta_sets[i]["ceil_regret_learned"] = ceil_regret(t, pred[offs[i]:offs[i + 1]] - margin)
+        meta_sets[i]["regret_doubling_rule"], meta_sets[i]["doubling_grid_point"] = doubling_regret(t)
     meta = {"mode": mode, "grid": list(GRID), "epochs": epochs, "train_loss": loss,
             "train_groups": int(F.shape[0]), "sets": meta_sets, "seconds": time.time() - t0,
             "features": "log2(1 + raw): h(s,t), deg(s), deg(t), w mean/std/min/max, n, m, |V_q|, |E_q|, "
@@ -278,6 +295,8 @@ def build_and_train(mode: str, out_dir: str = WEIGHTS_DIR, epochs: int = 600, lo
     if evaluate_sets:
         meta["eval"] = evaluate(mode, log=log, model=model)
         meta["eval_large"] = evaluate_large(mode, log=log, model=model)
+        if mode == "bidastar":
+            meta["eval_batch2048"] = evaluate_batch2048(log=log, model=model)
     path = save(model, mode, meta, out_dir)
     log(json.dumps({"saved": path, "train_loss": loss, "train_mae": meta["train_mae"], "margin": margin}))
     model.close()
@@ -300,8 +319,11 @@ def evaluate(mode: str, log=print, model=None) -> dict:
         feats, times, default = sweep(G, pairs, mode)
     y = model.predict(feats)
     lab = labels_from_times(times)
-    res = {"mode": mode, "eval_set": "road1024 near/mid/far (bench queries)", "groups": int(feats.shape[0]),
+    dr, dj = doubling_regret(times)
+    res = {"mode": mode, "eval_set": "road1024 benchmark graph (held out of training), its 1,000 near/mid/far "
+                                     "queries", "groups": int(feats.shape[0]),
            "regret_learned": regret(times, y), "regret_default": default_regret(times),
+           "regret_doubling_rule": dr, "doubling_grid_point": dj,
            "best_grid_hist": {str(j): int((lab == j).sum()) for j in GRID if (lab == j).any()},
            "pred_mean": float(y.mean())}
     if own:
@@ -325,9 +347,36 @@ def evaluate_large(mode: str, log=print, model=None, k: int = 96) -> dict:
     with ppsp.Graph.from_csr(g) as G:
         feats, times, default = sweep(G, pairs, mode, start=-4)
     y = model.predict(feats)
+    dr, dj = doubling_regret(times)
     res = {"mode": mode, "eval_set": f"road4096 serving graph, {k} random pairs", "groups": int(feats.shape[0]),
            "regret_learned": regret(times, y), "regret_default": default_regret(times),
-           "pred_mean": float(y.mean())}
+           "regret_doubling_rule": dr, "doubling_grid_point": dj, "pred_mean": float(y.mean())}
+    if own:
+        model.close()
+    log(json.dumps(res))
+    return res
+
+
+def evaluate_batch2048(log=print, model=None) -> dict:
+    """Regret on the 2,048-query batch of the 2048^2 road-like graph (random
+    pairs and a 32-clique answered as independent BiD-A* pairs, as the AUTO
+    strategy runs them; held out of training)."""
+    from workloads import config_workload
+
+    wl = config_workload(4)
+    g, pairs = wl["graph"], wl["batches"]["mixed"]
+    own = model is None
+    if own:
+        model = load_model("bidastar")
+    if model is None:
+        raise FileNotFoundError(weights_path("bidastar"))
+    with ppsp.Graph.from_csr(g) as G:
+        feats, times, default = sweep(G, pairs, "bidastar", start=-3, strategy="auto")
+    y = model.predict(feats)
+    dr, dj = doubling_regret(times)
+    res = {"mode": "bidastar", "eval_set": "road2048 batch of 2,048 queries (AUTO strategy)",
+           "groups": int(feats.shape[0]), "regret_learned": regret(times, y), "regret_default": default_regret(times),
+           "regret_doubling_rule": dr, "doubling_grid_point": dj, "pred_mean": float(y.mean())}
     if own:
         model.close()
     log(json.dumps(res))

@@ -68,8 +68,17 @@ def test_inference_matches_oracle_within_fp32_bound(count):
     y_ref, _ = omlp.forward(d, feats)
     bound = _fp32_bound(d, feats, 49, 193, 193)
     assert np.all(np.abs(y - y_ref) <= 2 * bound + 1e-30), np.max(np.abs(y - y_ref) / bound)
-    # the bound is far below any real error (a dropped term or transposed weight)
-    assert np.median(bound) < 1e-4 * np.median(np.abs(y_ref) + 1)
+    # the bound separates rounding from real mistakes: the oracle with a
+    # planted mistake (second-layer weights transposed, or the output bias
+    # dropped) lands outside it on most samples
+    for planted in ("W2T", "b3"):
+        bad = {k: np.array(v, copy=True) for k, v in d.items()}
+        if planted == "W2T":
+            bad["W2"] = bad["W2"].T.copy()
+        else:
+            bad["b3"][:] = 0.0
+        y_bad, _ = omlp.forward(bad, feats)
+        assert np.mean(np.abs(y_bad - y_ref) > 2 * bound) > 0.5, planted
     assert np.array_equal(m.params(), p)
     m.close()
 

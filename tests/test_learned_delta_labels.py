@@ -9,6 +9,7 @@ charges a prediction between two grid points the larger increment's time.
 
 import numpy as np
 
+from paper_2506_16488_gb300 import learned_delta as ld
 from paper_2506_16488_gb300.learned_delta import MARGINS, ceil_regret, default_regret, labels_from_times, regret
 
 GRID = (-2, -1, 0, 1)
@@ -44,3 +45,16 @@ def test_regret_measures():
 def test_margins_start_at_zero_and_grow():
     m = np.asarray(MARGINS)
     assert m[0] == 0.0 and np.all(np.diff(m) > 0) and m[-1] <= 2.0
+
+
+def test_doubling_rule_regret():
+    # three groups, grid points -1, 0, 1 (the last one never swept)
+    t = np.array([[2.0, 1.0, np.inf],
+                  [1.0, 3.0, np.inf],
+                  [4.0, 4.0, np.inf]])
+    grid = (-1, 0, 1)
+    # one increment for all: column totals 7 and 8, so -1 (7) against the
+    # per-group best 1 + 1 + 4 = 6
+    r, j = ld.doubling_regret(t, grid)
+    assert j == -1 and abs(r - (7.0 / 6.0 - 1.0)) < 1e-12
+    assert ld.doubling_regret(np.full((2, 3), np.inf), grid) == (None, None)
