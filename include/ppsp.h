@@ -344,8 +344,10 @@ ppsp_status ppsp_plan_device_bytes(const ppsp_plan* p, uint64_t* slot_bytes, uin
  * Device bytes of the slot one team of a batch allocates for groups of
  * `searches` searches (2 for a BiDS pair, 1 for an SSSP-based or
  * one-directional search, up to 64 for a Multi-BiDS group) with the given
- * distance width (32 or 64) and frontier policy, on a team smaller than the
- * whole GPU.  A batch plan holds one slot per team, and at most as many
+ * distance width (32 or 64) and frontier policy: the larger of the two
+ * sizes a team can take (a team that spans the plan's whole grid keeps a
+ * touched list for every entry of the range, a smaller team a quarter of it
+ * plus 4,096).  A batch plan holds one slot per team, and at most as many
  * teams as groups, so admission control can bound a batch's search memory
  * before creating its plan (host only, no device work).
  * Errors: INVALID_ARG.

@@ -1206,7 +1206,8 @@ ppsp_status ppsp_slot_bytes(const ppsp_graph* g, uint32_t searches, int32_t dist
     // the plan's layouts: a group of k searches spans n * 2^ceil(log2 k)
     // interleaved entries (k entries per vertex for pairs and singles)
     const u64 range = (u64)g->n << ceil_log2(searches);
-    const SlotCaps sc = slot_caps(range, frontier, false);
+    // the larger touched list of a team that spans the whole grid
+    const SlotCaps sc = slot_caps(range, frontier, true);
     *out = slot_alloc_bytes(dist_bits, sc.flat_cap, sc.qcap, sc.tcap);
     return PPSP_OK;
 }
