@@ -176,10 +176,6 @@ static __device__ bool team_sync(const TeamCtx& tc, const EngineArgs& a, u32* s_
 constexpr u32 QSTAGE = 1024;  // staged frontier appends per CTA and tile
 constexpr u32 TSTAGE = 512;   // staged touched-list appends per CTA and tile
 constexpr u32 PCAP = 1024;    // partner entries of a group cached in shared memory
-// relaxations of a pair group each thread keeps in flight (one-CTA path)
-#ifndef PPSP_RELAX_ILP
-#define PPSP_RELAX_ILP 2
-#endif
 
 constexpr u32 LR_NB = 32;  // buckets in the one-CTA ring
 
@@ -228,6 +224,12 @@ struct Smem {
     u32 lfar_fb, lfar_tgt, lspill, tov;
     u32 lrecov, lidle;  // spill recovered since the last processed bucket; decisions without one
     u32 lfar_after;     // far-list entries right after the last re-bucketing
+    // entries a warp with many edges hands to the whole CTA (process_local)
+    u32 fbeg[B];
+    u32 fdeg[B];
+    u64 fdd[B];
+    unsigned char fsi[B];
+    u32 ndefer;
     // step scalars
     u64 minkey_in, minkey_acc;
     u32 count, overflow, dir0, dir1, tile, flag, total, nitems, cert;
@@ -351,7 +353,7 @@ struct GCtx {
     bool pair;        // two searches, interleaved: both distances of v share 2*W bytes
     u32 n;
     // per-thread counters
-    u64 c_x, c_e, c_r, c_p, c_t;
+    u32 c_x, c_e, c_r, c_p, c_t;  // this group's counts (flushed at its end)
     // one-CTA path: this thread's net change of the per-direction entry
     // counts, added to the shared counts once per tile (flush_dir)
     int dc0, dc1;
@@ -1016,21 +1018,32 @@ constexpr u32 WARP_EDGES_MAX = 256;
 
 // One relaxation of a pair group without waiting for the old distance: the
 // pair just read decides success (a concurrent smaller write only leaves a
-// stale entry behind, which extraction drops).
-template <typename D, int B>
-__device__ __forceinline__ void relax_pair_nowait(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm,
-                                                  const LocalView<D, B>& L, u32 i, u64 d, uint2 ew) {
-    const u32 v2 = ew.x;
-    const u64 nd = d + (u64)ew.y;
-    if (bad_index(a, v2 < c.n, 4)) return;
-    const PotPre pp = pot_prefetch<D, B>(a, c, sm, v2, 0);  // pair: the term is indexed by vertex
+// stale entry behind, which extraction drops).  In two halves, so that a
+// lane can issue the loads of two edges before it waits for either:
+// pair_issue loads both distances of v2 and its potential, pair_finish
+// updates.
+template <typename D>
+struct PairLd {
     u64 x0, x1;
-    ld_pair(c.dist, v2, x0, x1);
+    PotPre pp;
+};
+
+template <typename D, int B>
+__device__ __forceinline__ PairLd<D> pair_issue(const EngineArgs& a, const GCtx<D>& c, const Smem<B>& sm, u32 v2) {
+    PairLd<D> r;
+    r.pp = pot_prefetch<D, B>(a, c, sm, v2, 0);  // pair: the term is indexed by vertex
+    ld_pair(c.dist, v2, r.x0, r.x1);
+    return r;
+}
+
+template <typename D, int B>
+__device__ __forceinline__ void pair_finish(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L,
+                                            u32 i, u32 v2, u64 nd, const PairLd<D>& r) {
     if (nd > DT<D>::MAXV) {
         atomicOr(a.err, ERRB_OVERFLOW);
         return;
     }
-    const u64 own = i ? x1 : x0, oth = i ? x0 : x1;
+    const u64 own = i ? r.x1 : r.x0, oth = i ? r.x0 : r.x1;
     if (nd >= own) return;
     const u32 f2 = (v2 << 1) | i;
     amin_dist(c.dist + f2, nd);
@@ -1038,9 +1051,57 @@ __device__ __forceinline__ void relax_pair_nowait(const EngineArgs& a, GCtx<D>& 
     if (own == DT<D>::INF) touch_local<D, B>(c, sm, f2);
     if (oth != DT<D>::INF) try_mu(a, c.G, sm, c.G.qbeg, nd + oth);
     i64 key, pv;
-    key_of<B>(c.G, sm, i, pot_resolve<D, B>(a, c, sm, i, v2, f2, pp), nd, key, pv);
+    key_of<B>(c.G, sm, i, pot_resolve<D, B>(a, c, sm, i, v2, f2, r.pp), nd, key, pv);
     if (pruned(pv, sm.bound[i])) return;
     insert_local<D, B>(c, sm, L, f2, i, key, nd);
+}
+
+// Owner of edge j of a warp's expansion (the first lane whose inclusive
+// degree prefix exceeds j) and that edge: its adjacency index, search and the
+// owner's distance.  Called by the full warp; valid only for j < wtot.
+struct WarpEdge {
+    u32 edge, si;
+    u64 d;
+};
+
+__device__ __forceinline__ WarpEdge warp_edge(u32 j, u32 incl, u32 xb0, u32 xex, u32 xsi, u64 xd) {
+    u32 o = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const u32 x = __shfl_sync(0xffffffffu, incl, o + step - 1);
+        if (x <= j) o += step;
+    }
+    WarpEdge w;
+    w.edge = __shfl_sync(0xffffffffu, xb0, o) + (j - __shfl_sync(0xffffffffu, xex, o));
+    w.si = __shfl_sync(0xffffffffu, xsi, o);
+    const u32 dl = __shfl_sync(0xffffffffu, (u32)xd, o);
+    const u32 dh = __shfl_sync(0xffffffffu, (u32)(xd >> 32), o);
+    w.d = ((u64)dh << 32) | dl;
+    return w;
+}
+
+// Relax up to two edges of this thread (edge index and search, the owner's
+// distance): both adjacency loads, then for pair groups both distance loads,
+// are issued before the first update waits on memory.
+template <typename D, int B>
+__device__ __forceinline__ void relax_two(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L,
+                                          bool va, u32 sa, u32 ga, u64 da, bool vb, u32 sb, u32 gb, u64 db) {
+    uint2 ea = make_uint2(0, 0), eb = make_uint2(0, 0);
+    if (va) ea = __ldg(adj<B>(a, sm, sa) + ga);
+    if (vb) eb = __ldg(adj<B>(a, sm, sb) + gb);
+    c.c_e += (va ? 1u : 0u) + (vb ? 1u : 0u);
+    if (c.pair) {
+        const bool pa = va && !bad_index(a, ea.x < c.n, 4);
+        const bool pb = vb && !bad_index(a, eb.x < c.n, 4);
+        PairLd<D> ra{}, rb{};
+        if (pa) ra = pair_issue<D, B>(a, c, sm, ea.x);
+        if (pb) rb = pair_issue<D, B>(a, c, sm, eb.x);
+        if (pa) pair_finish<D, B>(a, c, sm, L, sa, ea.x, da + (u64)ea.y, ra);
+        if (pb) pair_finish<D, B>(a, c, sm, L, sb, eb.x, db + (u64)eb.y, rb);
+    } else {
+        if (va) relax_local<D, B>(a, c, sm, L, sa, da, ea);
+        if (vb) relax_local<D, B>(a, c, sm, L, sb, db, eb);
+    }
 }
 
 // mode 0: entries of the current bucket (extract), spread over the warps
@@ -1093,9 +1154,6 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
                 }
                 if (!pruned(pv, sm.bound[i])) {
                     deg = b1 - b0;
-                    sm.beg[t] = b0;
-                    sm.si[t] = (unsigned char)i;
-                    sm.d[t] = d;
                     xb0 = b0;
                     xsi = i;
                     xd = d;
@@ -1119,137 +1177,62 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
         if (lane >= (u32)o) incl += y;
     }
     const u32 wtot = __shfl_sync(0xffffffffu, incl, 31);
-    if (!__syncthreads_or(wtot > WARP_EDGES_MAX)) {
-        PH_MARK(sm, 2);  // wait for the slowest extraction
-        // the warp expands its own entries: edge j belongs to the first lane
-        // whose inclusive prefix exceeds j
+    const bool many = wtot > WARP_EDGES_MAX;
+    if (!many) {
+        // the warp expands its own entries' edges, two per lane in flight:
+        // both edge loads, then both distance loads, before the first
+        // update waits on memory
         const u32 xex = incl - deg;
-        for (u32 j0 = 0; j0 < wtot; j0 += 32) {
-            const u32 j = j0 + lane;
-            u32 o = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const u32 x = __shfl_sync(0xffffffffu, incl, o + step - 1);
-                if (x <= j) o += step;
-            }
-            const u32 ob0 = __shfl_sync(0xffffffffu, xb0, o);
-            const u32 oex = __shfl_sync(0xffffffffu, xex, o);
-            const u32 osi = __shfl_sync(0xffffffffu, xsi, o);
-            const u32 odl = __shfl_sync(0xffffffffu, (u32)xd, o);
-            const u32 odh = __shfl_sync(0xffffffffu, (u32)(xd >> 32), o);
-            if (j < wtot && !bad_index(a, ob0 + (j - oex) < a.g.m && osi < c.G.scnt, 3)) {
-                const u64 od = ((u64)odh << 32) | odl;
-                const uint2 ew = __ldg(adj<B>(a, sm, osi) + ob0 + (j - oex));
-                ++c.c_e;
-                if (c.pair)
-                    relax_pair_nowait<D, B>(a, c, sm, L, osi, od, ew);
-                else
-                    relax_local<D, B>(a, c, sm, L, osi, od, ew);
-            }
+        for (u32 j0 = 0; j0 < wtot; j0 += 64) {
+            const u32 ja = j0 + lane, jb = j0 + 32 + lane;
+            const WarpEdge wa = warp_edge(ja, incl, xb0, xex, xsi, xd);
+            const WarpEdge wb = warp_edge(jb, incl, xb0, xex, xsi, xd);
+            const bool va = ja < wtot && !bad_index(a, wa.edge < a.g.m && wa.si < c.G.scnt, 3);
+            const bool vb = jb < wtot && !bad_index(a, wb.edge < a.g.m && wb.si < c.G.scnt, 3);
+            relax_two<D, B>(a, c, sm, L, va, wa.si, wa.edge, wa.d, vb, wb.si, wb.edge, wb.d);
         }
-        PH_MARK(sm, 3);  // thread 0's relaxations
-        flush_dir<D, B>(c, sm);
-        __syncthreads();
+    } else if (deg) {
+        // a warp with many edges (high-degree vertices) hands its entries to
+        // the whole CTA, after the step's closing barrier
+        const u32 k = atomicAdd(&sm.ndefer, 1u);  // < B: one entry per thread
+        sm.fbeg[k] = xb0;
+        sm.fsi[k] = (unsigned char)xsi;
+        sm.fdd[k] = xd;
+        sm.fdeg[k] = deg;
+    }
+    PH_MARK(sm, 3);  // thread 0's relaxations
+    flush_dir<D, B>(c, sm);
+    if (!__syncthreads_or(many)) {
         PH_MARK(sm, 4);  // wait for the slowest relaxation
         return;
     }
-    // some warp holds many edges (high-degree vertices): the CTA shares them
+    // the deferred entries (threads 0 .. nd - 1): degree scan, owner table,
+    // then the CTA relaxes their edges together
+    const u32 nd = sm.ndefer;
+    const u32 fdeg = t < nd ? sm.fdeg[t] : 0u;
     u32 total;
-    const u32 excl = block_excl_scan<B>(deg, sm, &total, deg > OWN_MAXDEG);
-    sm.pre[t] = excl;  // entries are spread over the threads: the prefix covers all of them
-    if (deg) write_owner<B>(sm, t, excl, deg);
+    const u32 excl = block_excl_scan<B>(fdeg, sm, &total, fdeg > OWN_MAXDEG);
+    sm.pre[t] = excl;  // threads past the deferred entries hold the total
+    if (fdeg) write_owner<B>(sm, t, excl, fdeg);
+    if (t == 0) sm.ndefer = 0;  // every thread read it before the scan's barriers
     __syncthreads();
-    PH_MARK(sm, 2);  // scan, including the wait for the slowest extraction
-    if (c.pair) {
-        // pair groups: RX edges per thread at a time, their loads and atomics
-        // issued together (instruction-level parallelism on the dependent
-        // edge -> distance -> atomicMin chain)
-        constexpr int RX = (B >= 1024) ? 1 : PPSP_RELAX_ILP;  // 1,024 threads: 64 registers
-        for (u32 e0 = t; e0 < total; e0 += RX * B) {
-            u32 v2[RX], si[RX], f2[RX];
-            u64 nd[RX], own[RX], oth[RX], old[RX];
-            PotPre pp[RX];
-            bool ok[RX];
-#pragma unroll
-            for (int k = 0; k < RX; ++k) {
-                const u32 e = e0 + k * B;
-                ok[k] = e < total;
-                v2[k] = 0;
-                nd[k] = DT<D>::INF;
-                si[k] = 0;
-                if (ok[k]) {
-                    const u32 lo = edge_owner<B>(sm, e, B);
-                    if (bad_index(a, lo < B && sm.beg[lo] + (e - sm.pre[lo]) < a.g.m, 6)) {
-                        ok[k] = false;
-                        continue;
-                    }
-                    const uint2 ew = __ldg(adj<B>(a, sm, sm.si[lo]) + sm.beg[lo] + (e - sm.pre[lo]));
-                    v2[k] = ew.x;
-                    si[k] = sm.si[lo];
-                    nd[k] = sm.d[lo] + (u64)ew.y;
-                    ++c.c_e;
-                }
-            }
-            PH_MARK(sm, 7);  // edge search + edge loads issued
-#pragma unroll
-            for (int k = 0; k < RX; ++k) {
-                pp[k].pv = make_int2(0, 0);
-                pp[k].mw = 0;
-                if (ok[k]) {
-                    pp[k] = pot_prefetch<D, B>(a, c, sm, v2[k], 0);  // pair: the term is indexed by vertex
-                    u64 x0, x1;
-                    ld_pair(c.dist, v2[k], x0, x1);
-                    own[k] = si[k] ? x1 : x0;
-                    oth[k] = si[k] ? x0 : x1;
-                }
-            }
-            PH_MARK(sm, 8);  // edge loads returned, distance loads issued
-#pragma unroll
-            for (int k = 0; k < RX; ++k) {
-                old[k] = 0;
-                if (ok[k]) {
-                    if (nd[k] > DT<D>::MAXV) {
-                        atomicOr(a.err, ERRB_OVERFLOW);
-                        ok[k] = false;
-                    } else if (nd[k] < own[k]) {
-                        // WriteMin without waiting for the old value: the
-                        // distance just read decides success (a concurrent
-                        // smaller write only makes this entry stale, and
-                        // extraction drops stale entries)
-                        f2[k] = (v2[k] << 1) | si[k];
-                        amin_dist(c.dist + f2[k], nd[k]);
-                        old[k] = own[k];
-                    } else {
-                        ok[k] = false;
-                    }
-                }
-            }
-            PH_MARK(sm, 9);  // distances returned, atomics issued
-#pragma unroll
-            for (int k = 0; k < RX; ++k) {
-                if (!ok[k] || nd[k] >= old[k]) continue;
-                ++c.c_r;
-                if (old[k] == DT<D>::INF) touch_local<D, B>(c, sm, f2[k]);
-                if (oth[k] != DT<D>::INF) try_mu(a, c.G, sm, c.G.qbeg, nd[k] + oth[k]);
-                i64 key, pv;
-                key_of<B>(c.G, sm, si[k], pot_resolve<D, B>(a, c, sm, si[k], v2[k], f2[k], pp[k]), nd[k], key,
-                          pv);
-                if (pruned(pv, sm.bound[si[k]])) continue;
-                insert_local<D, B>(c, sm, L, f2[k], si[k], key, nd[k]);
-            }
-            PH_MARK(sm, 10);  // atomics returned, potentials, mu, insertions
+    for (u32 e0 = t; e0 < total; e0 += 2 * B) {
+        const u32 ea = e0, eb = e0 + B;
+        u32 la = 0, lb = 0, ga = 0, gb = 0;
+        bool va = ea < total, vb = eb < total;
+        if (va) {
+            la = edge_owner<B>(sm, ea, nd);
+            ga = sm.fbeg[la] + (ea - sm.pre[la]);
+            va = !bad_index(a, la < nd && ga < a.g.m && sm.fsi[la] < c.G.scnt, 6);
         }
-    } else {
-        for (u32 e = t; e < total; e += B) {
-            const u32 lo = edge_owner<B>(sm, e, B);
-            const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
-            if (bad_index(a, lo < B && edge < a.g.m, 6)) continue;
-            const uint2 ew = __ldg(adj<B>(a, sm, sm.si[lo]) + edge);
-            ++c.c_e;
-            relax_local<D, B>(a, c, sm, L, sm.si[lo], sm.d[lo], ew);
+        if (vb) {
+            lb = edge_owner<B>(sm, eb, nd);
+            gb = sm.fbeg[lb] + (eb - sm.pre[lb]);
+            vb = !bad_index(a, lb < nd && gb < a.g.m && sm.fsi[lb] < c.G.scnt, 6);
         }
+        relax_two<D, B>(a, c, sm, L, va, va ? sm.fsi[la] : 0u, ga, va ? sm.fdd[la] : 0ull, vb,
+                        vb ? sm.fsi[lb] : 0u, gb, vb ? sm.fdd[lb] : 0ull);
     }
-    PH_MARK(sm, 3);  // thread 0's relaxations
     flush_dir<D, B>(c, sm);
     __syncthreads();
     PH_MARK(sm, 4);  // wait for the slowest relaxation
@@ -1337,6 +1320,7 @@ __device__ u64 run_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 nword
         sm.lrecov = 0;
         sm.lidle = 0;
         sm.lfar_after = 0;
+        sm.ndefer = 0;
         sm.cnt_dir[0] = sm.cnt_dir[1] = 0;
     }
     __syncthreads();
@@ -1634,7 +1618,7 @@ __device__ bool find_paths(const EngineArgs& a, const TeamCtx& tc, GCtx<D>& c, S
 // registers.
 template <typename D, int B, bool LOCAL>
 __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev& slot, u32 gi,
-                          Smem<B>& sm, u64* cnt_acc) {
+                          Smem<B>& sm) {
     const u32 t = threadIdx.x;
     GCtx<D> c;
     c.G = a.groups[gi];
@@ -1980,20 +1964,28 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
             }
         }
     }
-    // order of EngineCounters: extracted, edges, relaxed, pushed, rounds,
-    // groups, searches, touched, dense_rounds
-    cnt_acc[0] += c.c_x;
-    cnt_acc[1] += c.c_e;
-    cnt_acc[2] += c.c_r;
-    cnt_acc[3] += c.c_p;
-    cnt_acc[7] += c.c_t;
-    if (a.group_ns && t == 0 && tc.rank == 0) a.group_ns[gi] = global_ns() - t_start;
-    if (t == 0 && tc.rank == 0) {
-        cnt_acc[4] += rounds;
-        cnt_acc[5] += 1;
-        cnt_acc[6] += G.scnt;
-        cnt_acc[8] += dense_rounds;
+    // this group's counts, one atomic per warp and counter (order of
+    // EngineCounters: extracted, edges, relaxed, pushed, rounds, groups,
+    // searches, touched, dense_rounds)
+    if (a.counters) {
+        unsigned long long* cp = &a.counters->extracted;
+        const u32 mine[5] = {c.c_x, c.c_e, c.c_r, c.c_p, c.c_t};
+        const int at[5] = {0, 1, 2, 3, 7};
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            u64 x = mine[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if ((t & 31u) == 0 && x) atomicAdd(cp + at[k], (unsigned long long)x);
+        }
+        if (t == 0 && tc.rank == 0) {
+            atomicAdd(cp + 4, (unsigned long long)rounds);
+            atomicAdd(cp + 5, 1ull);
+            atomicAdd(cp + 6, (unsigned long long)G.scnt);
+            if (dense_rounds) atomicAdd(cp + 8, (unsigned long long)dense_rounds);
+        }
     }
+    if (a.group_ns && t == 0 && tc.rank == 0) a.group_ns[gi] = global_ns() - t_start;
     return team_sync(tc, a, &sm.flag);
 }
 
@@ -2037,8 +2029,6 @@ __global__ void __launch_bounds__(B, (EngineMinBlocks<B, LOCAL>::value))
     tc.expect = tc.size + (never ? 1u : 0u);
     const u32 qid = a.team_queue[tc.team];
     const SlotDev slot = a.slots[tc.team];
-    u64 acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-
     for (;;) {
         if (threadIdx.x == 0) {
             if (tc.rank == 0) {
@@ -2054,18 +2044,7 @@ __global__ void __launch_bounds__(B, (EngineMinBlocks<B, LOCAL>::value))
         const u32 gi = sm.group;
         if (!team_sync(tc, a, &sm.flag)) break;  // everyone has read ts->group
         if (gi == NONE) break;
-        if (!run_group<D, B, LOCAL>(a, tc, slot, gi, sm, acc)) break;
-    }
-    // counters
-    if (a.counters) {
-        unsigned long long* cp = &a.counters->extracted;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            u64 x = acc[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if ((threadIdx.x & 31) == 0 && x) atomicAdd(cp + k, (unsigned long long)x);
-        }
+        if (!run_group<D, B, LOCAL>(a, tc, slot, gi, sm)) break;
     }
 }
 
