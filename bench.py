@@ -357,6 +357,8 @@ def _choose_opts(G, pairs, mode, args, world):
     if args.config == 5:
         base["dist_bits"] = 64  # the serving graph's configuration keeps uint64 distances
     if args.strategy != "tuned" or world > 1:
+        if args.block_threads:
+            base["block_threads"] = args.block_threads
         return base, None
     t0 = time.perf_counter()
     res = autotune.tune(G, pairs, mode, base=base, reps=2, budget_s=args.tune_budget)
@@ -688,6 +690,9 @@ def main():
     ap.add_argument("--plain-teams", type=int, nargs="*", default=[1, 16, 0],
                     help="team sizes tried for the plain one-query-at-a-time baseline (0 = all CTAs)")
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on resident CTAs (profiling)")
+    ap.add_argument("--block-threads", type=int, default=0, choices=[0, 256, 512, 1024],
+                    help="threads per CTA of the headline plan with a fixed strategy (0 = the library's choice; "
+                         "profiling the tuner's launch)")
     ap.add_argument("--compare", nargs="*", default=["multi", "multi_potential"],
                     choices=["multi", "multi_potential", "auto", "plain_star", "sssp", "vc"],
                     help="also time these batch strategies on the same batch (one run each)")
