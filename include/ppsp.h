@@ -61,7 +61,7 @@ enum {
 };
 
 /* Graph flags. */
-enum { PPSP_UNDIRECTED = 1u };
+enum { PPSP_UNDIRECTED = 1u, PPSP_KEEP_VERTEX_ORDER = 2u };
 
 /* Frontier representation policy (App. B "Sparse-Dense Optimization").
  * AUTO: a group run by one CTA keeps its frontier as Delta*-stepping buckets
@@ -216,6 +216,14 @@ const char* ppsp_last_error_detail(void);
  *            target searches in-edges (Sec. 4.4: searches forward from sources,
  *            backward from targets; Multi-BiDS groups pair them bipartitely).
  *            VC-SSSP covers the bipartite query graph (Konig).
+ *            PPSP_KEEP_VERTEX_ORDER: keep the caller's vertex order on the
+ *            device.  By default a graph with coordinates is stored in the
+ *            order of a Hilbert curve over its coordinates, so that vertices
+ *            near each other in the plane share cache lines of the
+ *            adjacency, potential and distance arrays (a search's frontier
+ *            is a compact region).  The renumbering is internal: every call
+ *            takes and returns the caller's vertex ids (pairs, paths,
+ *            potential coordinates), and distances do not depend on it.
  * Inputs are copied; the caller may free them after the call.  On success
  * *out owns device memory until ppsp_graph_destroy.
  * Errors: INVALID_ARG (null pointers, n or m out of range), BAD_GRAPH

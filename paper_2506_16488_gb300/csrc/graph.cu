@@ -163,6 +163,64 @@ static bool check_symmetric(u64 n, const u64* off, const u32* tgt, const u32* w)
     return ok;
 }
 
+// Position of the point (x, y) of a 2^bits x 2^bits lattice along the
+// Hilbert curve that fills it: at each scale the quadrant adds its rank in
+// the curve's visiting order (lower-left, upper-left, upper-right,
+// lower-right for the unrotated curve) times the quadrant's size, and the
+// point is rotated or reflected into the orientation the curve has inside
+// that quadrant.
+static u64 hilbert_rank(u32 x, u32 y, u32 bits) {
+    const u32 side = 1u << bits;
+    u64 d = 0;
+    for (u32 q = side >> 1; q > 0; q >>= 1) {
+        const u32 rx = (x & q) ? 1u : 0u, ry = (y & q) ? 1u : 0u;
+        d += (u64)q * q * ((3u * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = side - 1 - x;
+                y = side - 1 - y;
+            }
+            const u32 tmp = x;
+            x = y;
+            y = tmp;
+        }
+    }
+    return d;
+}
+
+// Device order of a graph with coordinates: vertices sorted by the Hilbert
+// rank of their coordinates on a 2^16 x 2^16 lattice over the bounding
+// square (ties by id).  Returns false (order kept) for non-finite
+// coordinates.  perm[v] = device id of caller vertex v; inv = its inverse.
+static bool locality_order(u64 n, const float* xy, std::vector<u32>& perm, std::vector<u32>& inv) {
+    double xmin = INFINITY, ymin = INFINITY, xmax = -INFINITY, ymax = -INFINITY;
+    for (u64 v = 0; v < n; ++v) {
+        const double x = xy[2 * v], y = xy[2 * v + 1];
+        if (!std::isfinite(x) || !std::isfinite(y)) return false;
+        xmin = std::min(xmin, x);
+        xmax = std::max(xmax, x);
+        ymin = std::min(ymin, y);
+        ymax = std::max(ymax, y);
+    }
+    const double span = std::max(xmax - xmin, ymax - ymin);
+    const double scale = span > 0.0 ? 65535.0 / span : 0.0;
+    std::vector<u64> key(n);
+    for (u64 v = 0; v < n; ++v) {
+        const u32 qx = (u32)std::min(65535.0, std::max(0.0, ((double)xy[2 * v] - xmin) * scale));
+        const u32 qy = (u32)std::min(65535.0, std::max(0.0, ((double)xy[2 * v + 1] - ymin) * scale));
+        key[v] = (hilbert_rank(qx, qy, 16) << 32) | v;  // the rank is below 2^32
+    }
+    std::sort(key.begin(), key.end());
+    perm.resize(n);
+    inv.resize(n);
+    for (u64 i = 0; i < n; ++i) {
+        const u32 v = (u32)(key[i] & 0xFFFFFFFFull);
+        inv[i] = v;
+        perm[v] = (u32)i;
+    }
+    return true;
+}
+
 SlotCaps slot_caps(u64 range, int frontier, bool whole_gpu) {
     u64 fc = std::max<u64>(range, 64);
     fc = (fc + 63) & ~63ull;
@@ -336,6 +394,34 @@ ppsp_status ppsp_graph_create(uint64_t n, uint64_t m, const uint64_t* offsets, c
     auto g = std::make_unique<ppsp_graph>();
     g->n = n;
     g->m = m;
+    // device order: along a Hilbert curve over the coordinates, so that a
+    // search's compact frontier region maps to few cache lines; the arrays
+    // below are renumbered copies and every call maps ids at the boundary
+    std::vector<u64> off_r;
+    std::vector<u32> tgt_r, w_r;
+    std::vector<float> xy_r;
+    if (coords && !(flags & PPSP_KEEP_VERTEX_ORDER) && n > 1 && locality_order(n, coords, g->perm, g->inv)) {
+        off_r.resize(n + 1);
+        tgt_r.resize(m);
+        w_r.resize(m);
+        xy_r.resize(2 * n);
+        off_r[0] = 0;
+        for (u64 i = 0; i < n; ++i) {
+            const u64 v = g->inv[i];
+            u64 o = off_r[i];
+            for (u64 e = offsets[v]; e < offsets[v + 1]; ++e, ++o) {
+                tgt_r[o] = g->perm[targets[e]];
+                w_r[o] = weights[e];
+            }
+            off_r[i + 1] = o;
+            xy_r[2 * i] = coords[2 * v];
+            xy_r[2 * i + 1] = coords[2 * v + 1];
+        }
+        offsets = off_r.data();
+        targets = tgt_r.data();
+        weights = w_r.data();
+        coords = xy_r.data();
+    }
     ppsp_graph_info& info = g->info;
     info.n = n;
     info.m = m;
@@ -468,7 +554,14 @@ ppsp_status ppsp_graph_get_info(const ppsp_graph* g, ppsp_graph_info* out) {
 ppsp_status ppsp_potential_coords(const ppsp_graph* g, int64_t* out) {
     if (!g || !out) return PPSP_ERR_INVALID_ARG;
     if (!g->info.has_coords) return PPSP_ERR_NO_COORDS;
-    memcpy(out, g->pc_host.data(), 2 * g->n * sizeof(int64_t));
+    if (g->perm.empty()) {
+        memcpy(out, g->pc_host.data(), 2 * g->n * sizeof(int64_t));
+    } else {
+        for (u64 v = 0; v < g->n; ++v) {  // caller order
+            out[2 * v] = g->pc_host[2 * (u64)g->perm[v]];
+            out[2 * v + 1] = g->pc_host[2 * (u64)g->perm[v] + 1];
+        }
+    }
     return PPSP_OK;
 }
 
@@ -488,6 +581,13 @@ ppsp_status ppsp_potential_eval(ppsp_graph* g, uint32_t anchor, const uint32_t* 
         PPSP_CUDA_TRY(cudaMalloc(&g->d_scratch_u32, count * 4));
         PPSP_CUDA_TRY(cudaMalloc(&g->d_scratch_i64, count * 8));
         g->scratch_cap = count;
+    }
+    std::vector<u32> mapped;
+    if (!g->perm.empty()) {  // device ids (an id out of range stays out of range: the kernel answers -1)
+        mapped.resize(count);
+        for (u64 k = 0; k < count; ++k) mapped[k] = vertices[k] < g->n ? g->perm[vertices[k]] : vertices[k];
+        vertices = mapped.data();
+        anchor = g->perm[anchor];
     }
     PPSP_CUDA_TRY(cudaMemcpy(g->d_scratch_u32, vertices, count * 4, cudaMemcpyHostToDevice));
     ppsp_status st = launch_potential_eval(g->dev(), anchor, g->d_scratch_u32, count, g->d_scratch_i64, 0);

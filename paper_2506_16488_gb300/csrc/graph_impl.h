@@ -49,6 +49,9 @@ struct ppsp_graph {
     int pot_shift = 0;
     ppsp_graph_info info{};
     std::vector<uint64_t> deg;     // host copy of degrees (features, schedules)
+    // internal vertex order: perm[caller id] = device id, inv[device id] =
+    // caller id (both empty when the caller's order is kept)
+    std::vector<ppsp::u32> perm, inv;
     // slot pool
     std::multimap<ppsp::SlotKey, std::unique_ptr<ppsp::Slot>> pool;
     std::mutex mu;

@@ -366,6 +366,13 @@ static ppsp_status plan_create_impl(ppsp_graph* g, const uint32_t* pairs, uint64
     const u64 n = g->n;
     for (u64 q = 0; q < 2 * k; ++q)
         if (pairs[q] >= n) return PPSP_ERR_INVALID_ARG;
+    // the graph's device order (caller ids in, device ids from here on)
+    std::vector<u32> pairs_dev;
+    if (!g->perm.empty()) {
+        pairs_dev.resize(2 * k);
+        for (u64 q = 0; q < 2 * k; ++q) pairs_dev[q] = g->perm[pairs[q]];
+        pairs = pairs_dev.data();
+    }
 
     auto P = std::make_unique<ppsp_plan>();
     P->g = g;
@@ -1289,9 +1296,14 @@ static ppsp_status run_host(ppsp_graph* g, const uint32_t* pairs, uint64_t k, co
                 const u32 qe = P->map[q];
                 len = plen[qe];
                 if (len <= cap && len <= P->path_off[qe + 1] - P->path_off[qe] && hp->buf) {
+                    // device ids back to the caller's
                     const u32* src = pbuf.data() + P->path_off[qe];
-                    const bool fwd = (P->qedge_ends[qe].first == s);
-                    for (u64 x = 0; x < len; ++x) dst[x] = fwd ? src[x] : src[len - 1 - x];
+                    const u32 s_dev = g->perm.empty() ? s : g->perm[s];
+                    const bool fwd = (P->qedge_ends[qe].first == s_dev);
+                    for (u64 x = 0; x < len; ++x) {
+                        const u32 y = fwd ? src[x] : src[len - 1 - x];
+                        dst[x] = g->inv.empty() ? y : g->inv[y];
+                    }
                 } else {
                     small = true;
                 }

@@ -31,6 +31,7 @@ FRONTIER = {"auto": 0, "sparse": 1, "dense": 2}
 LAYOUT = {"auto": 0, "interleaved": 1, "stacked": 2}
 STRATEGY = {"multi": 0, "plain_star": 1, "plain": 2, "sssp": 3, "vc": 4, "auto": 5}
 UNDIRECTED = 1
+KEEP_VERTEX_ORDER = 2
 DEBUG_BARRIER_NEVER_RELEASES = 1
 MLP_FEATURES = 12
 MLP_PARAMS = 5081
@@ -237,7 +238,7 @@ def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, 
 class Graph:
     """Device-resident CSR graph (ppsp_graph_create / ppsp_graph_destroy)."""
 
-    def __init__(self, offsets, targets, weights, coords=None, undirected: bool = True):
+    def __init__(self, offsets, targets, weights, coords=None, undirected: bool = True, keep_order: bool = False):
         lib = load()
         self._off = np.ascontiguousarray(offsets, dtype=np.uint64)
         tgt = np.ascontiguousarray(targets, dtype=np.uint32)
@@ -246,7 +247,8 @@ class Graph:
         n = self._off.shape[0] - 1
         h = ctypes.c_void_p()
         st = lib.ppsp_graph_create(n, tgt.shape[0], _ptr(self._off), _ptr(tgt), _ptr(w), _ptr(xy),
-                                   UNDIRECTED if undirected else 0, ctypes.byref(h))
+                                   (UNDIRECTED if undirected else 0) | (KEEP_VERTEX_ORDER if keep_order else 0),
+                                   ctypes.byref(h))
         _check(st, "ppsp_graph_create")
         self._h = h
         self.n = n
@@ -255,10 +257,12 @@ class Graph:
         self._models = {}
 
     @classmethod
-    def from_csr(cls, g, undirected: bool = True, with_coords: bool = True):
+    def from_csr(cls, g, undirected: bool = True, with_coords: bool = True, keep_order: bool = False):
         """From an object with offsets, targets, weights and coords (a
-        workloads.CSRGraph)."""
-        return cls(g.offsets, g.targets, g.weights, g.coords if with_coords else None, undirected)
+        workloads.CSRGraph).  keep_order keeps the caller's vertex order on
+        the device (default: a Hilbert-curve order over the coordinates;
+        ids are mapped at the boundary either way)."""
+        return cls(g.offsets, g.targets, g.weights, g.coords if with_coords else None, undirected, keep_order)
 
     def close(self):
         """Destroy the graph; its open plans are destroyed first (a plan
