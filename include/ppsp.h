@@ -208,7 +208,12 @@ const char* ppsp_last_error_detail(void);
  *   offsets  host uint64[n+1], offsets[0] = 0, non-decreasing, offsets[n] = m
  *   targets  host uint32[m], every id < n
  *   weights  host uint32[m]
- *   coords   host float[2n] (x, y per vertex) or NULL; needed by the A* modes
+ *   coords   host float[2n] (x, y per vertex) or NULL; needed by the A* modes.
+ *            With coordinates the library also keeps the adjacency as 16-byte
+ *            records (target, weight, integer potential coordinates of the
+ *            target: another 16m bytes, 32m for a directed graph), which the
+ *            searches with a potential read instead of gathering the
+ *            target's coordinates separately
  *   flags    PPSP_UNDIRECTED: the CSR is symmetric with equal weights both ways
  *            (validated; the bidirectional modes search backwards on the same CSR).
  *            Without it the graph is directed: the library also keeps its

@@ -335,6 +335,12 @@ template <int B>
 __device__ __forceinline__ const uint2* adj(const EngineArgs& a, const Smem<B>& sm, u32 i) {
     return sm.sdir[i] ? a.g.edges_t : a.g.edges;
 }
+// The same rows as 16-byte records carrying P(target) (graphs with
+// coordinates, searches with a potential).
+template <int B>
+__device__ __forceinline__ const int4* adj16(const EngineArgs& a, const Smem<B>& sm, u32 i) {
+    return sm.sdir[i] ? a.g.edges_t_pc : a.g.edges_pc;
+}
 
 // ----------------------------------------------------------------------------
 // per-group context
@@ -358,6 +364,7 @@ struct GCtx {
     // counts, added to the shared counts once per tile (flush_dir)
     int dc0, dc1;
     u32* err;         // the device error word (checked builds)
+    bool adj16;       // relaxations read 16-byte edge records with P(target)
     // heuristic memoization (Sec. 5): the potential term of each entry,
     // stored as term + 2^31 (0 = not evaluated yet), indexed by vertex for
     // pair groups (the two searches' terms are opposite) and by flat index
@@ -403,6 +410,14 @@ struct PotPre {
     int2 pv;
     u32 mw;
 };
+
+// Potential coordinates that came with an edge record (no load).
+__device__ __forceinline__ PotPre pot_given(int2 q) {
+    PotPre p;
+    p.pv = q;
+    p.mw = 0;
+    return p;
+}
 
 template <typename D, int B>
 __device__ __forceinline__ PotPre pot_prefetch(const EngineArgs& a, const GCtx<D>& c, const Smem<B>& sm, u32 v,
@@ -647,12 +662,13 @@ __device__ __forceinline__ void after_relax(const EngineArgs& a, GCtx<D>& c, Sme
 
 template <typename D, int B>
 __device__ __forceinline__ void relax(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 i, u64 d,
-                                      uint2 ew) {
+                                      uint2 ew, int2 q) {
     const u32 v2 = ew.x;
     const u64 nd = d + (u64)ew.y;
     if (bad_index(a, v2 < c.n, 4)) return;
-    // prefetch, overlaps the distance load
-    const PotPre pp = pot_prefetch<D, B>(a, c, sm, v2, c.pair ? ((v2 << 1) | i) : flat_of(c.G, c.n, v2, i));
+    // prefetch, overlaps the distance load (or P(v2) came with the edge)
+    const PotPre pp = c.adj16 ? pot_given(q)
+                              : pot_prefetch<D, B>(a, c, sm, v2, c.pair ? ((v2 << 1) | i) : flat_of(c.G, c.n, v2, i));
     if (nd > DT<D>::MAXV) {
         atomicOr(a.err, ERRB_OVERFLOW);
         return;
@@ -801,9 +817,17 @@ __device__ void process_items(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, u32 
         const u32 lo = edge_owner<B>(sm, e, cnt);
         const u32 edge = sm.beg[lo] + (e - sm.pre[lo]);
         if (bad_index(a, lo < cnt && edge < a.g.m, 7)) continue;
-        const uint2 ew = __ldg(adj<B>(a, sm, sm.si[lo]) + edge);
+        uint2 ew;
+        int2 q = make_int2(0, 0);
+        if (c.adj16) {
+            const int4 r = __ldg(adj16<B>(a, sm, sm.si[lo]) + edge);
+            ew = make_uint2((u32)r.x, (u32)r.y);
+            q = make_int2(r.z, r.w);
+        } else {
+            ew = __ldg(adj<B>(a, sm, sm.si[lo]) + edge);
+        }
         ++c.c_e;
-        relax<D, B>(a, c, sm, sm.si[lo], sm.d[lo], ew);
+        relax<D, B>(a, c, sm, sm.si[lo], sm.d[lo], ew, q);
     }
     flush_stage<D, B>(c, sm);
 }
@@ -942,12 +966,12 @@ __device__ __forceinline__ void touch_local(GCtx<D>& c, Smem<B>& sm, u32 f) {
 
 template <typename D, int B>
 __device__ __forceinline__ void relax_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L,
-                                            u32 i, u64 d, uint2 ew) {
+                                            u32 i, u64 d, uint2 ew, int2 q) {
     const u32 v2 = ew.x;
     const u64 nd = d + (u64)ew.y;
     if (bad_index(a, v2 < c.n, 4)) return;
     const u32 f2 = c.pair ? ((v2 << 1) | i) : flat_of(c.G, c.n, v2, i);
-    const PotPre pp = pot_prefetch<D, B>(a, c, sm, v2, f2);
+    const PotPre pp = c.adj16 ? pot_given(q) : pot_prefetch<D, B>(a, c, sm, v2, f2);
     if (nd > DT<D>::MAXV) {
         atomicOr(a.err, ERRB_OVERFLOW);
         return;
@@ -1032,9 +1056,11 @@ struct PairLd {
 };
 
 template <typename D, int B>
-__device__ __forceinline__ PairLd<D> pair_issue(const EngineArgs& a, const GCtx<D>& c, const Smem<B>& sm, u32 v2) {
+__device__ __forceinline__ PairLd<D> pair_issue(const EngineArgs& a, const GCtx<D>& c, const Smem<B>& sm, u32 v2,
+                                                int2 q) {
     PairLd<D> r;
-    r.pp = pot_prefetch<D, B>(a, c, sm, v2, 0);  // pair: the term is indexed by vertex
+    // pair: the term is indexed by vertex; with 16-byte records P(v2) came with the edge
+    r.pp = c.adj16 ? pot_given(q) : pot_prefetch<D, B>(a, c, sm, v2, 0);
     ld_pair(c.dist, v2, r.x0, r.x1);
     return r;
 }
@@ -1090,20 +1116,34 @@ template <typename D, int B>
 __device__ __forceinline__ void relax_two(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L,
                                           bool va, u32 sa, u32 ga, u64 da, bool vb, u32 sb, u32 gb, u64 db) {
     uint2 ea = make_uint2(0, 0), eb = make_uint2(0, 0);
-    if (va) ea = __ldg(adj<B>(a, sm, sa) + ga);
-    if (vb) eb = __ldg(adj<B>(a, sm, sb) + gb);
+    int2 qa = make_int2(0, 0), qb = make_int2(0, 0);
+    if (c.adj16) {
+        if (va) {
+            const int4 r = __ldg(adj16<B>(a, sm, sa) + ga);
+            ea = make_uint2((u32)r.x, (u32)r.y);
+            qa = make_int2(r.z, r.w);
+        }
+        if (vb) {
+            const int4 r = __ldg(adj16<B>(a, sm, sb) + gb);
+            eb = make_uint2((u32)r.x, (u32)r.y);
+            qb = make_int2(r.z, r.w);
+        }
+    } else {
+        if (va) ea = __ldg(adj<B>(a, sm, sa) + ga);
+        if (vb) eb = __ldg(adj<B>(a, sm, sb) + gb);
+    }
     c.c_e += (va ? 1u : 0u) + (vb ? 1u : 0u);
     if (c.pair) {
         const bool pa = va && !bad_index(a, ea.x < c.n, 4);
         const bool pb = vb && !bad_index(a, eb.x < c.n, 4);
         PairLd<D> ra{}, rb{};
-        if (pa) ra = pair_issue<D, B>(a, c, sm, ea.x);
-        if (pb) rb = pair_issue<D, B>(a, c, sm, eb.x);
+        if (pa) ra = pair_issue<D, B>(a, c, sm, ea.x, qa);
+        if (pb) rb = pair_issue<D, B>(a, c, sm, eb.x, qb);
         if (pa) pair_finish<D, B>(a, c, sm, L, sa, ea.x, da + (u64)ea.y, ra);
         if (pb) pair_finish<D, B>(a, c, sm, L, sb, eb.x, db + (u64)eb.y, rb);
     } else {
-        if (va) relax_local<D, B>(a, c, sm, L, sa, da, ea);
-        if (vb) relax_local<D, B>(a, c, sm, L, sb, db, eb);
+        if (va) relax_local<D, B>(a, c, sm, L, sa, da, ea, qa);
+        if (vb) relax_local<D, B>(a, c, sm, L, sb, db, eb, qb);
     }
 }
 
@@ -1637,6 +1677,7 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
     c.pair = (G.mode == GM_BIDIR && G.scnt == 2 && G.layout == PPSP_LAYOUT_INTERLEAVED && G.kshift == 1);
     c.memo = (a.memo && a.g.pc != nullptr) ? slot.memo : nullptr;
     c.err = a.err;
+    c.adj16 = false;
     if (t == 0) {
         const SearchDev s0 = a.searches[G.sbeg];
         const SearchDev sl = a.searches[G.sbeg + G.scnt - 1];
@@ -1675,6 +1716,9 @@ __device__ bool run_group(const EngineArgs& a, const TeamCtx& tc, const SlotDev&
         for (u32 k = t; k < np; k += B) sm.pcache[k] = a.partners[s0.pbeg + k];
     }
     __syncthreads();
+    // with a potential (and no memo), relaxations take P(target) from
+    // 16-byte edge records when the graph has them
+    c.adj16 = a.g.edges_pc != nullptr && sm.pot_any != 0 && c.memo == nullptr;
 
     // Init (Table 2): delta_i[q_i] = 0 and <q_i, i> in F for every search;
     // mu = inf (0 when both ends coincide).

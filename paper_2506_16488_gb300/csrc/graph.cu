@@ -482,6 +482,8 @@ ppsp_status ppsp_graph_create(uint64_t n, uint64_t m, const uint64_t* offsets, c
         cudaFree(g->d_off_t);
         cudaFree(g->d_edges_t);
         cudaFree(g->d_pc);
+        cudaFree(g->d_edges_pc);
+        cudaFree(g->d_edges_t_pc);
         return e == cudaErrorMemoryAllocation ? PPSP_ERR_OOM : PPSP_ERR_CUDA;
     };
     if ((ce = cudaMalloc(&g->d_off, (n + 1) * 4)) != cudaSuccess) return fail(ce, "cudaMalloc(off)");
@@ -491,6 +493,7 @@ ppsp_status ppsp_graph_create(uint64_t n, uint64_t m, const uint64_t* offsets, c
     if (m && (ce = cudaMemcpy(g->d_edges, ed.data(), m * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(ce, "cudaMemcpy(edges)");
     info.device_bytes = (n + 1) * 4 + m * 8;
+    std::vector<uint2> edt;  // transpose records (directed graphs)
     if (!info.undirected) {
         // transpose (in-edges, each row sorted by source): backward searches
         // from a target and path walks of forward searches follow it
@@ -498,7 +501,7 @@ ppsp_status ppsp_graph_create(uint64_t n, uint64_t m, const uint64_t* offsets, c
         for (u64 e = 0; e < m; ++e) ++offt[targets[e] + 1];
         for (u64 v = 0; v < n; ++v) offt[v + 1] += offt[v];
         std::vector<u32> fill(offt.begin(), offt.end() - 1);
-        std::vector<uint2> edt(m);
+        edt.resize(m);
         for (u64 u = 0; u < n; ++u)
             for (u64 e = offsets[u]; e < offsets[u + 1]; ++e) edt[fill[targets[e]]++] = make_uint2((u32)u, weights[e]);
         if ((ce = cudaMalloc(&g->d_off_t, (n + 1) * 4)) != cudaSuccess) return fail(ce, "cudaMalloc(off_t)");
@@ -525,6 +528,30 @@ ppsp_status ppsp_graph_create(uint64_t n, uint64_t m, const uint64_t* offsets, c
             return fail(ce, "cudaMemcpy(pc)");
         info.device_bytes += n * 8;
     }
+    if (coords) {
+        // the adjacency again as (target, weight, P(target)): a relaxation's
+        // potential coordinates arrive with its edge record
+        const bool scaled = g->pot_scale > 0.0;
+        auto rec = [&](u32 v, u32 w) {
+            return make_int4((int)v, (int)w, scaled ? (int)g->pc_host[2 * (u64)v] : 0,
+                             scaled ? (int)g->pc_host[2 * (u64)v + 1] : 0);
+        };
+        std::vector<int4> e16(std::max<u64>(1, m));
+        for (u64 e = 0; e < m; ++e) e16[e] = rec(targets[e], weights[e]);
+        if ((ce = cudaMalloc(&g->d_edges_pc, std::max<u64>(1, m) * 16)) != cudaSuccess)
+            return fail(ce, "cudaMalloc(edges_pc)");
+        if (m && (ce = cudaMemcpy(g->d_edges_pc, e16.data(), m * 16, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(ce, "cudaMemcpy(edges_pc)");
+        info.device_bytes += m * 16;
+        if (!info.undirected) {
+            for (u64 e = 0; e < m; ++e) e16[e] = rec(edt[e].x, edt[e].y);
+            if ((ce = cudaMalloc(&g->d_edges_t_pc, std::max<u64>(1, m) * 16)) != cudaSuccess)
+                return fail(ce, "cudaMalloc(edges_t_pc)");
+            if (m && (ce = cudaMemcpy(g->d_edges_t_pc, e16.data(), m * 16, cudaMemcpyHostToDevice)) != cudaSuccess)
+                return fail(ce, "cudaMemcpy(edges_t_pc)");
+            info.device_bytes += m * 16;
+        }
+    }
     *out = g.release();
     return PPSP_OK;
 }
@@ -539,6 +566,8 @@ void ppsp_graph_destroy(ppsp_graph* g) {
     cudaFree(g->d_off_t);
     cudaFree(g->d_edges_t);
     cudaFree(g->d_pc);
+    cudaFree(g->d_edges_pc);
+    cudaFree(g->d_edges_t_pc);
     cudaFree(g->d_scratch_u32);
     cudaFree(g->d_scratch_i64);
     cudaGetLastError();

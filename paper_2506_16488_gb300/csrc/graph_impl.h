@@ -41,6 +41,8 @@ struct ppsp_graph {
     uint64_t n = 0, m = 0;
     ppsp::u32* d_off = nullptr;
     uint2* d_edges = nullptr;
+    int4* d_edges_pc = nullptr;    // (target, weight, P(target)) when the graph has coordinates
+    int4* d_edges_t_pc = nullptr;  // the same for the transpose of a directed graph
     ppsp::u32* d_off_t = nullptr;  // transpose of a directed graph (null when undirected)
     uint2* d_edges_t = nullptr;
     int2* d_pc = nullptr;
@@ -69,6 +71,8 @@ struct ppsp_graph {
         g.off_t = d_off_t ? d_off_t : d_off;
         g.edges_t = d_edges_t ? d_edges_t : d_edges;
         g.pc = d_pc;
+        g.edges_pc = d_edges_pc;
+        g.edges_t_pc = d_edges_t_pc ? d_edges_t_pc : d_edges_pc;
         g.n = (ppsp::u32)n;
         g.pot_shift = (ppsp::u32)pot_shift;
         g.m = (ppsp::u32)m;

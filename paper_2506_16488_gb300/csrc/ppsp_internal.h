@@ -45,6 +45,12 @@ struct GraphDev {
     const u32* off_t;     // [n+1] transpose (in-edges); the same arrays as off / edges when undirected
     const uint2* edges_t; // [m] (source, weight)
     const int2* pc;       // [n] integer potential coordinates, or null
+    // graphs with coordinates: the adjacency again as 16-byte records
+    // (target, weight, P(target).x, P(target).y), so that a relaxation gets
+    // the target's potential coordinates with its edge instead of a second,
+    // random load; null otherwise
+    const int4* edges_pc;
+    const int4* edges_t_pc;
     u32 n;
     u32 pot_shift;        // F: h = isqrt(d2 >> 2F)
     u32 m;                // adjacency entries (bounds of checked builds)
