@@ -448,8 +448,8 @@ ppsp_status ppsp_graph_set_delta_model(ppsp_graph* g, int32_t mode, ppsp_delta_m
  *   stream      cudaStream_t or NULL
  * The call waits for its stream before returning the status.  All calls share
  * the one array: calls that overlap on the GPU race and must not be issued.
- * The first call on a device resolves the array's address and initialises it;
- * make that call before any stream capture.  Errors: INVALID_ARG (null
+ * The first call on a device resolves the array's address and initialises it.
+ * Errors: INVALID_ARG (null
  * pointers, n above the limit, ids >= n, d_offsets not 4-byte aligned,
  * d_edges or d_dist_out not 8-byte aligned), UNSUPPORTED (a device on which
  * fewer than two engine CTAs fit), CUDA, TIMEOUT, OVERFLOW.

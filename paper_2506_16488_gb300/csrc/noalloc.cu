@@ -12,8 +12,7 @@
 //  * every call uses the same array; calls that overlap on the GPU (from two
 //    streams or two host threads) race and must not be issued;
 //  * the first call on a device resolves the array's device address
-//    (cudaGetSymbolAddress) and fills it; make that first call before any
-//    stream capture;
+//    (cudaGetSymbolAddress) and fills it;
 //  * the search leaves the array clean (distances infinite, bitmaps zero), and
 //    the per-call state is cleared at the start of every call.
 #include <algorithm>
