@@ -1045,10 +1045,11 @@ constexpr u32 WARP_EDGES_MAX = 256;
 
 // One relaxation of a pair group without waiting for the old distance: the
 // pair just read decides success (a concurrent smaller write only leaves a
-// stale entry behind, which extraction drops).  In two halves, so that a
-// lane can issue the loads of two edges before it waits for either:
-// pair_issue loads both distances of v2 and its potential, pair_finish
-// updates.
+// stale entry behind, which extraction drops).  In parts, so that a lane
+// can issue the loads of two edges before it waits for either and a warp can
+// pack its successes: pair_issue loads both distances of v2 (and its
+// potential unless the edge record carried it), pair_try tests and writes
+// the distance, pair_success does the rest.
 template <typename D>
 struct PairLd {
     u64 x0, x1;
@@ -1065,24 +1066,53 @@ __device__ __forceinline__ PairLd<D> pair_issue(const EngineArgs& a, const GCtx<
     return r;
 }
 
+// The cheap half of a pair relaxation: overflow check, the success test
+// against the distance just read, and the WriteMin (not waited for).  On
+// success returns true with the flat index, the other search's distance and
+// whether the entry left infinity.
 template <typename D, int B>
-__device__ __forceinline__ void pair_finish(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L,
-                                            u32 i, u32 v2, u64 nd, const PairLd<D>& r) {
+__device__ __forceinline__ bool pair_try(const EngineArgs& a, GCtx<D>& c, u32 i, u32 v2, u64 nd, const PairLd<D>& r,
+                                         u32& f2, u64& oth, bool& fresh) {
     if (nd > DT<D>::MAXV) {
         atomicOr(a.err, ERRB_OVERFLOW);
-        return;
+        return false;
     }
-    const u64 own = i ? r.x1 : r.x0, oth = i ? r.x0 : r.x1;
-    if (nd >= own) return;
-    const u32 f2 = (v2 << 1) | i;
+    const u64 own = i ? r.x1 : r.x0;
+    if (nd >= own) return false;
+    oth = i ? r.x0 : r.x1;
+    f2 = (v2 << 1) | i;
+    fresh = own == DT<D>::INF;
     amin_dist(c.dist + f2, nd);
+    return true;
+}
+
+// The rest of a successful pair relaxation: touched list, mu, key, prune,
+// insertion.
+template <typename D, int B>
+__device__ __forceinline__ void pair_success(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L,
+                                             u32 f2, u64 nd, u64 oth, bool fresh, const PotPre& pp) {
+    const u32 i = f2 & 1u, v2 = f2 >> 1;
     ++c.c_r;
-    if (own == DT<D>::INF) touch_local<D, B>(c, sm, f2);
+    if (fresh) touch_local<D, B>(c, sm, f2);
     if (oth != DT<D>::INF) try_mu(a, c.G, sm, c.G.qbeg, nd + oth);
     i64 key, pv;
-    key_of<B>(c.G, sm, i, pot_resolve<D, B>(a, c, sm, i, v2, f2, r.pp), nd, key, pv);
+    key_of<B>(c.G, sm, i, pot_resolve<D, B>(a, c, sm, i, v2, f2, pp), nd, key, pv);
     if (pruned(pv, sm.bound[i])) return;
     insert_local<D, B>(c, sm, L, f2, i, key, nd);
+}
+
+// Position of the k-th (from 0) set bit of m, for k < popc(m).
+__device__ __forceinline__ u32 nth_set_bit(u32 m, u32 k) {
+    u32 pos = 0;
+#pragma unroll
+    for (u32 step = 16; step > 0; step >>= 1)
+        if ((u32)__popc(m & ((1u << (pos + step)) - 1u)) <= k) pos += step;
+    return pos;
+}
+
+__device__ __forceinline__ u64 shfl_u64(u64 x, u32 src) {
+    const u32 lo = __shfl_sync(0xffffffffu, (u32)x, src), hi = __shfl_sync(0xffffffffu, (u32)(x >> 32), src);
+    return ((u64)hi << 32) | lo;
 }
 
 // Owner of edge j of a warp's expansion (the first lane whose inclusive
@@ -1111,7 +1141,9 @@ __device__ __forceinline__ WarpEdge warp_edge(u32 j, u32 incl, u32 xb0, u32 xex,
 
 // Relax up to two edges of this thread (edge index and search, the owner's
 // distance): both adjacency loads, then for pair groups both distance loads,
-// are issued before the first update waits on memory.
+// are issued before the first update waits on memory.  Called by full warps
+// (a warp-uniform number of times): pair groups pack the warp's successful
+// relaxations with ballots and shuffles.
 template <typename D, int B>
 __device__ __forceinline__ void relax_two(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, const LocalView<D, B>& L,
                                           bool va, u32 sa, u32 ga, u64 da, bool vb, u32 sb, u32 gb, u64 db) {
@@ -1139,8 +1171,35 @@ __device__ __forceinline__ void relax_two(const EngineArgs& a, GCtx<D>& c, Smem<
         PairLd<D> ra{}, rb{};
         if (pa) ra = pair_issue<D, B>(a, c, sm, ea.x, qa);
         if (pb) rb = pair_issue<D, B>(a, c, sm, eb.x, qb);
-        if (pa) pair_finish<D, B>(a, c, sm, L, sa, ea.x, da + (u64)ea.y, ra);
-        if (pb) pair_finish<D, B>(a, c, sm, L, sb, eb.x, db + (u64)eb.y, rb);
+        // the success tests and WriteMins of both edges, then the warp's
+        // successes (about 40% of its edges) packed into as few passes of
+        // the heavier rest as they fill: one pass instead of one per edge
+        u32 fa = 0, fb = 0;
+        u64 nda = da + (u64)ea.y, ndb = db + (u64)eb.y, otha = 0, othb = 0;
+        bool fra = false, frb = false;
+        const bool oka = pa && pair_try<D, B>(a, c, sa, ea.x, nda, ra, fa, otha, fra);
+        const bool okb = pb && pair_try<D, B>(a, c, sb, eb.x, ndb, rb, fb, othb, frb);
+        const u32 lane = threadIdx.x & 31u;
+        const u32 ma = __ballot_sync(0xffffffffu, oka), mb = __ballot_sync(0xffffffffu, okb);
+        const u32 na = __popc(ma), ntot = na + __popc(mb);
+        for (u32 k0 = 0; k0 < ntot; k0 += 32) {
+            const u32 k = k0 + lane;
+            const bool has = k < ntot, from_a = k < na;
+            const u32 src = has ? (from_a ? nth_set_bit(ma, k) : nth_set_bit(mb, k - na)) : 0u;
+            const u32 f_a = __shfl_sync(0xffffffffu, fa, src), f_b = __shfl_sync(0xffffffffu, fb, src);
+            const u64 nd_a = shfl_u64(nda, src), nd_b = shfl_u64(ndb, src);
+            const u64 ot_a = shfl_u64(otha, src), ot_b = shfl_u64(othb, src);
+            const u32 fl = __shfl_sync(0xffffffffu, (fra ? 1u : 0u) | (frb ? 2u : 0u), src);
+            PotPre pp;
+            const int px_a = __shfl_sync(0xffffffffu, ra.pp.pv.x, src), px_b = __shfl_sync(0xffffffffu, rb.pp.pv.x, src);
+            const int py_a = __shfl_sync(0xffffffffu, ra.pp.pv.y, src), py_b = __shfl_sync(0xffffffffu, rb.pp.pv.y, src);
+            const u32 mw_a = __shfl_sync(0xffffffffu, ra.pp.mw, src), mw_b = __shfl_sync(0xffffffffu, rb.pp.mw, src);
+            pp.pv = from_a ? make_int2(px_a, py_a) : make_int2(px_b, py_b);
+            pp.mw = from_a ? mw_a : mw_b;
+            if (has)
+                pair_success<D, B>(a, c, sm, L, from_a ? f_a : f_b, from_a ? nd_a : nd_b, from_a ? ot_a : ot_b,
+                                   (fl & (from_a ? 1u : 2u)) != 0, pp);
+        }
     } else {
         if (va) relax_local<D, B>(a, c, sm, L, sa, da, ea, qa);
         if (vb) relax_local<D, B>(a, c, sm, L, sb, db, eb, qb);
@@ -1259,8 +1318,9 @@ __device__ void process_local(const EngineArgs& a, GCtx<D>& c, Smem<B>& sm, cons
     if (fdeg) write_owner<B>(sm, t, excl, fdeg);
     if (t == 0) sm.ndefer = 0;  // every thread read it before the scan's barriers
     __syncthreads();
-    for (u32 e0 = t; e0 < total; e0 += 2 * B) {
-        const u32 ea = e0, eb = e0 + B;
+    // warp-uniform trip count: relax_two packs a warp's successes with shuffles
+    for (u32 w0 = t & ~31u; w0 < total; w0 += 2 * B) {
+        const u32 ea = w0 + (t & 31u), eb = ea + B;
         u32 la = 0, lb = 0, ga = 0, gb = 0;
         bool va = ea < total, vb = eb < total;
         if (va) {
