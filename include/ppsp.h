@@ -371,6 +371,18 @@ ppsp_status ppsp_slot_bytes(const ppsp_graph* g, uint32_t searches, int32_t dist
 /* 1 if the plan's last run replayed a captured CUDA graph, else 0. */
 ppsp_status ppsp_plan_uses_graph(const ppsp_plan* p, int32_t* out);
 
+/*
+ * The device vertex order ppsp_graph_create gives a graph with these
+ * coordinates (host only, no graph, no device work): vertices sorted by their
+ * position along a Hilbert curve over a 2^16 x 2^16 lattice spanning the
+ * bounding square of the coordinates (ties by id).
+ *   coords    host float[2n], (x, y) per vertex
+ *   perm_out  host uint32[n], caller-owned: perm_out[v] = device id of v
+ * Errors: INVALID_ARG (null pointers, n = 0 or n >= 2^32), UNSUPPORTED
+ * (non-finite coordinates: the graph keeps the caller's order).
+ */
+ppsp_status ppsp_vertex_order(uint64_t n, const float* coords, uint32_t* perm_out);
+
 /* Source selection of the SSSP-based batch strategies (Sec. 4.3), host only
  * (no device work, usable without a GPU).
  *   pairs      host array of k (s, t) vertex-id pairs (uint32, row-major k x 2)

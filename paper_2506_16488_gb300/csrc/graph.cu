@@ -574,6 +574,18 @@ void ppsp_graph_destroy(ppsp_graph* g) {
     delete g;
 }
 
+ppsp_status ppsp_vertex_order(uint64_t n, const float* coords, uint32_t* perm_out) {
+    if (!coords || !perm_out || n == 0 || n >= 0xFFFFFFFFull) return PPSP_ERR_INVALID_ARG;
+    if (n == 1) {
+        perm_out[0] = 0;
+        return PPSP_OK;
+    }
+    std::vector<u32> perm, inv;
+    if (!locality_order(n, coords, perm, inv)) return PPSP_ERR_UNSUPPORTED;
+    memcpy(perm_out, perm.data(), n * sizeof(u32));
+    return PPSP_OK;
+}
+
 ppsp_status ppsp_graph_get_info(const ppsp_graph* g, ppsp_graph_info* out) {
     if (!g || !out) return PPSP_ERR_INVALID_ARG;
     *out = g->info;

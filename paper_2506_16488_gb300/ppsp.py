@@ -150,6 +150,7 @@ def load(build_if_missing: bool = False):
             "ppsp_plan_device_bytes": (S, [p, p, p, p]),
             "ppsp_slot_bytes": (S, [p, u32, i32, i32, p]),
             "ppsp_batch_sources": (S, [p, u64, i32, u32, p, p, p]),
+            "ppsp_vertex_order": (S, [u64, p, p]),
             "ppsp_delta_model_create": (S, [p, p]),
             "ppsp_delta_model_destroy": (None, [p]),
             "ppsp_delta_model_get_params": (S, [p, p]),
@@ -197,6 +198,15 @@ def batch_sources(pairs, strategy: str | int = "vc", undirected: bool = True, re
     if return_dirs:
         return out[:k], int(n.value), dirs[:k]
     return out[:k], int(n.value)
+
+
+def vertex_order(coords) -> np.ndarray:
+    """perm[v] = the device id ppsp_graph_create gives vertex v of a graph
+    with these coordinates (float [n, 2]; host only)."""
+    xy = np.ascontiguousarray(coords, dtype=np.float32).reshape(-1, 2)
+    out = np.zeros(xy.shape[0], dtype=np.uint32)
+    _check(load().ppsp_vertex_order(xy.shape[0], _ptr(xy), _ptr(out)), "ppsp_vertex_order")
+    return out
 
 
 def make_options(mode: str | int = "bids", dist_bits: int = 32, delta: int = 0, frontier="auto",
