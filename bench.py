@@ -389,7 +389,9 @@ def extra_config3(args, peak, peak_kind, flush, stream):
         assert np.array_equal(got_m, got)
         res["multi"] = {"value": k / (ms[0] / 1000.0), "unit": "queries/s", "ms": ms[0],
                         "gteps": cnt["edges"] / ms[0] / 1e6, "searches": cnt["searches"]}
-        res["plain"] = _plain(G, pairs, got, args.plain_queries // 4, [1, 0], stream, mode=mode)
+        # one query at a time on 16 CTAs or on all of them (one CTA per query
+        # measured about 10x slower than all on this graph)
+        res["plain"] = _plain(G, pairs, got, args.plain_queries // 4, [16, 0], stream, mode=mode)
     res["speedup_vs_plain"] = res["auto"]["value"] / res["plain"]["value"]
     res["cpu_baseline"] = cpu_baseline(g, pairs, labels, per_stratum=4)
     return res
@@ -557,7 +559,7 @@ def run_ours(args):
     # plain: one query at a time (Plain-BiDS), with the default Delta and
     # with the same Delta rule as the batched run
     default_delta = max(1, int(round(G.info()["w_mean"])))
-    plain = _plain(G, pairs, got, args.plain_queries, args.plain_teams, stream, mode=mode,
+    plain = _plain(G, pairs, got, args.plain_queries, args.plain_default_teams, stream, mode=mode,
                    delta=args.delta or default_delta)
     plain["delta"] = f"default {default_delta}" if not args.delta else f"fixed {args.delta}"
     plain_same = _plain(G, pairs, got, args.plain_queries, args.plain_teams, stream, mode=mode,
@@ -687,6 +689,9 @@ def main():
     ap.add_argument("--queries", type=int, default=0, help="strided subset of the batch (profiling)")
     ap.add_argument("--plain-queries", type=int, default=100,
                     help="plain baseline: strided subset of the batch, answered one at a time")
+    ap.add_argument("--plain-default-teams", type=int, nargs="*", default=[16, 0],
+                    help="team sizes tried for the plain baseline with the default Delta (0 = all CTAs; one CTA "
+                         "answers about one query per second there, so it is not tried by default)")
     ap.add_argument("--plain-teams", type=int, nargs="*", default=[1, 16, 0],
                     help="team sizes tried for the plain one-query-at-a-time baseline (0 = all CTAs)")
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on resident CTAs (profiling)")
